@@ -1,0 +1,221 @@
+"""Python access to the plain FP64 CPU oracle (``fea_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module; the engine never
+does.  The oracle shares no code with the CUDA engine: it is compiled from
+its own C source with gcc, and its inputs are plain numpy arrays (typically
+from ``paper_1805_03949_gb300.meshgen``).
+
+Every function follows the assembly loop of the paper (Alg. "sequential
+assembly", Sec. 2.1.1) over the square local CSR system of Sec. 3.1; see the
+header of ``fea_oracle.c`` for the element formulations.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fea_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OP_DIFFUSION, OP_ELASTICITY = 0, 1
+NODES = {0: 4, 1: 5, 2: 6, 3: 8}
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [_SRC] + [os.path.join(_HERE, f) for f in sorted(os.listdir(_HERE))
+                     if f.endswith(".c") and f != "fea_oracle.c"]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp] + srcs + ["-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _lib.oracle_pattern.restype = _i64
+            _lib.oracle_pattern.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p]
+            _lib.oracle_expand_pattern.restype = None
+            _lib.oracle_expand_pattern.argtypes = [_i64, _i32, _p, _p, _p, _p]
+            _lib.oracle_assemble.restype = _i64
+            _lib.oracle_assemble.argtypes = [_i64, _i64, _p, _p, _p, _p, _i32, _i32, _p, _p, _p, _p, _p, _p, _p]
+            _lib.oracle_assemble_rows.restype = _i64
+            _lib.oracle_assemble_rows.argtypes = [_i64, _i64, _p, _p, _p, _p, _i32, _i32, _p, _i64, _p, _i64,
+                                                  _p, _p, _p, _p, _p, _p]
+            _lib.oracle_element.restype = _i32
+            _lib.oracle_element.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p]
+            _lib.oracle_quadrature.restype = _i32
+            _lib.oracle_quadrature.argtypes = [_i32, _i32, _p, _p]
+            _lib.oracle_shape.restype = _i32
+            _lib.oracle_shape.argtypes = [_i32, _p, _p, _p]
+            for name, (rt, at) in _extra_signatures().items():
+                f = getattr(_lib, name)
+                f.restype = rt
+                f.argtypes = at
+        return _lib
+
+
+def _extra_signatures():
+    return {}
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class InvertedElement(RuntimeError):
+    def __init__(self, elem):
+        super().__init__(f"element {elem} has detJ <= 0 at a quadrature point")
+        self.elem = elem
+
+
+def op_params(op: int, **kw) -> np.ndarray:
+    if op == OP_DIFFUSION:
+        return np.array([kw.get("k0", 1.0), kw.get("k2", 0.0), kw.get("source", 1.0)], dtype=np.float64)
+    f = kw.get("body_force", (1.0, 1.0, 1.0))
+    return np.array([kw.get("young", 1.0), kw.get("poisson", 0.3), f[0], f[1], f[2]], dtype=np.float64)
+
+
+def quadrature(etype: int, tet_rule: int = 1):
+    pts = np.zeros((8, 3)); w = np.zeros(8)
+    nq = lib().oracle_quadrature(etype, tet_rule, _ptr(pts), _ptr(w))
+    return pts[:nq].copy(), w[:nq].copy()
+
+
+def shape(etype: int, p):
+    p = _c(p, np.float64)
+    N = np.zeros(8); dN = np.zeros((8, 3))
+    nn = lib().oracle_shape(etype, _ptr(p), _ptr(N), _ptr(dN))
+    return N[:nn].copy(), dN[:nn].copy()
+
+
+def element(etype: int, X, op: int = OP_DIFFUSION, tet_rule: int = 1, **kw):
+    """Element matrix, RHS and magnitude sums of one element with node coordinates X [nn,3]."""
+    X = _c(X, np.float64)
+    d = 1 if op == OP_DIFFUSION else 3
+    n = NODES[etype] * d
+    Ae = np.zeros((n, n)); be = np.zeros(n); Se = np.zeros((n, n)); Sb = np.zeros(n)
+    params = op_params(op, **kw)
+    rc = lib().oracle_element(etype, tet_rule, op, _ptr(params), _ptr(X), _ptr(Ae), _ptr(be), _ptr(Se), _ptr(Sb))
+    if rc:
+        raise InvertedElement(-1)
+    return Ae, be, Se, Sb
+
+
+def pattern(mesh, ndof: int = 1):
+    """CSR pattern (scalar, ndof interleaved dofs per node) and the node rank map.
+
+    Returns (row_ptr int64 [n*ndof+1], col_idx int32 [nnz], node_map int32
+    [sum n_e^2]).  node_map[off(e) + a*n_e + b] is the rank k of node
+    conn[e][b] among the sorted neighbours of node conn[e][a]; the scalar entry
+    of (dof d*i+c, dof d*j+c') sits at row_ptr[d*i+c] + d*k + c'.
+    """
+    L = lib()
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    n = mesh.n_nodes
+    rp = np.zeros(n + 1, dtype=np.int64)
+    nnz = L.oracle_pattern(n, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(rp), None, None)
+    if nnz < 0:
+        raise ValueError("bad mesh")
+    col = np.zeros(nnz, dtype=np.int32)
+    nn = np.diff(off)
+    nmap = np.zeros(int((nn * nn).sum()), dtype=np.int32)
+    L.oracle_pattern(n, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(rp), _ptr(col), _ptr(nmap))
+    if ndof == 1:
+        return rp, col, nmap
+    rps = np.zeros(n * ndof + 1, dtype=np.int64)
+    cols = np.zeros(nnz * ndof * ndof, dtype=np.int32)
+    L.oracle_expand_pattern(n, ndof, _ptr(rp), _ptr(col), _ptr(rps), _ptr(cols))
+    return rps, cols, nmap
+
+
+def assemble(mesh, op: int = OP_DIFFUSION, tet_rule: int = 1, pat=None, **kw):
+    """Assemble A (CSR values) and b in element-index order, with magnitude sums.
+
+    Returns dict(row_ptr, col_idx, node_map, A, b, SA, Sb).
+    """
+    d = 1 if op == OP_DIFFUSION else 3
+    if pat is None:
+        pat = pattern(mesh, d)
+    rps, cols, nmap = pat
+    A = np.zeros(cols.shape[0]); SA = np.zeros_like(A)
+    b = np.zeros(mesh.n_nodes * d); Sb = np.zeros_like(b)
+    params = op_params(op, **kw)
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64)
+    rc = lib().oracle_assemble(mesh.n_nodes, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords),
+                               op, tet_rule, _ptr(params), _ptr(rps), _ptr(nmap),
+                               _ptr(A), _ptr(b), _ptr(SA), _ptr(Sb))
+    if rc < 0:
+        raise InvertedElement(-rc - 1)
+    return dict(row_ptr=rps, col_idx=cols, node_map=nmap, A=A, b=b, SA=SA, Sb=Sb)
+
+
+def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_cols: int = 512, **kw):
+    """All dof rows of the requested nodes, summed over every element in index order.
+
+    Returns a list with, per node, dict(cols (node neighbours), vals [d, deg*d],
+    svals, b [d], sb [d]).
+    """
+    d = 1 if op == OP_DIFFUSION else 3
+    req = _c(nodes, np.int32)
+    r = len(req)
+    cols = np.zeros((r, max_cols), dtype=np.int32)
+    deg = np.zeros(r, dtype=np.int64)
+    vals = np.zeros(r * max_cols * d * d); svals = np.zeros_like(vals)
+    bv = np.zeros(r * d); sbv = np.zeros_like(bv)
+    params = op_params(op, **kw)
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64)
+    rc = lib().oracle_assemble_rows(mesh.n_nodes, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords),
+                                    op, tet_rule, _ptr(params), r, _ptr(req), max_cols, _ptr(cols), _ptr(deg),
+                                    _ptr(vals), _ptr(svals), _ptr(bv), _ptr(sbv))
+    if rc == -1:
+        raise ValueError("row wider than max_cols")
+    if rc < 0:
+        raise InvertedElement(-rc - 1)
+    out = []
+    for t in range(r):
+        k = int(deg[t])
+        base = t * max_cols * d * d
+        out.append(dict(cols=cols[t, :k].copy(),
+                        vals=vals[base:base + d * k * d].reshape(d, k * d).copy(),
+                        svals=svals[base:base + d * k * d].reshape(d, k * d).copy(),
+                        b=bv[t * d:(t + 1) * d].copy(), sb=sbv[t * d:(t + 1) * d].copy()))
+    return out
+
+
+def err_metric(a, ref, S):
+    """max |a - ref| / S over entries with S > 0, and whether S == 0 entries match exactly.
+
+    S is the oracle's magnitude sum: the same formula with every factor taken
+    in absolute value, the scale of the a-priori rounding error bound.
+    """
+    a = np.asarray(a, dtype=np.float64); ref = np.asarray(ref, dtype=np.float64); S = np.asarray(S)
+    pos = S > 0
+    err = float(np.max(np.abs(a[pos] - ref[pos]) / S[pos])) if pos.any() else 0.0
+    zeros_ok = bool(np.all(a[~pos] == 0.0) and np.all(ref[~pos] == 0.0))
+    return err, zeros_ok
