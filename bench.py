@@ -1,0 +1,365 @@
+"""Benchmark of the finite element assembly engine on one GB300 (one rank per GPU).
+
+Workload (default): 3D linear elasticity on hex8, a 128^3 unit cube with
+interior nodes jittered by U(-0.2h, 0.2h) (PCG64 seed 2): 2,097,152 elements,
+2,146,689 nodes, 513,599,625 scalar nonzeros, 2x2x2 Gauss.  This is the
+synthetic stand-in for the paper's large mechanics meshes (the Iter and
+respiratory meshes, Sec. 2.1.5 / 2.2.2, are not available).
+
+One step = one ``fea_assemble`` call (zero A and b, integrate every element,
+scatter into the CSR system) on a mesh, pattern and map already resident in
+HBM.  The metric is assembled elements per second; the comparator is the
+plain per-type FP64 atomic assembly on the same GPU in the same run.  A (4.1
+GB) is far larger than L2 (129 MB), so no L2 flush is needed between steps.
+
+Under torchrun each rank assembles its own copy of the workload (the
+partial-row decomposition of Sec. 3.1 needs no communication during
+assembly): weak scaling, value = all ranks' elements / max rank time.
+
+``--impl reference`` times the CPU oracle (single thread, element-index
+order) on a bounded slab of the same mesh and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_FP64_TFLOPS = 1.25     # GB300 FP64 (nominal, profiling recipe)
+NOMINAL_FP32_TFLOPS = 80.5     # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, same GB300"
+
+
+def _peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload and algorithmic counts
+# ---------------------------------------------------------------------------
+
+def c2_mesh(n=128):
+    from paper_1805_03949_gb300 import meshgen as mg
+    return mg.hex_cube(n, 0.2, 2)
+
+
+def algorithmic_bytes(n_nodes, n_elems, nnz, nn=8, ndof=3):
+    """Bytes one assembly must move: A and b written once, inputs read once.
+
+    per element: conn 4*nn, node_map 4*nn^2; per node: coords 24, row_ptr 8*ndof,
+    b 8*ndof; per nonzero: A 8.
+    """
+    return 8 * nnz + n_nodes * (24 + 8 * ndof + 8 * ndof) + n_elems * (4 * nn + 4 * nn * nn)
+
+
+def algorithmic_flops_hex_elasticity(n_elems, nq=8, nn=8):
+    """FP arithmetic of hex8 elasticity with the symmetric row blocks (a <= b).
+
+    per point: Jacobian 7*9 FMA, cofactors 9 mul + 9 FMA, det 1 mul + 2 FMA,
+    1 reciprocal, gradients 8*9 FMA + 24 mul, w*detJ 1 mul (FMA = 2 flop);
+    per (a <= b) block and point: 3 FMA (dot) + 18 FMA + 3 add; per (a, point)
+    6 mul; RHS 3 FMA per (a, point).
+    """
+    geo = 2 * 63 + (9 + 2 * 9) + (1 + 2 * 2) + 1 + (2 * 72 + 24) + 1
+    blocks = nn * (nn + 1) // 2
+    integ = blocks * (2 * 3 + 2 * 18 + 3) + nn * 6 + nn * 2 * 3
+    return n_elems * nq * (geo + integ)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1805_03949_gb300 import fea
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    mesh = c2_mesh(args.n)
+    t0 = time.perf_counter()
+    sysm = fea.System.from_mesh(mesh, 3, device=dev, with_cols=True)
+    torch.cuda.synchronize()
+    pattern_s = time.perf_counter() - t0
+    nnz = sysm.A.numel()
+    E, N = sysm.n_elems, sysm.n_nodes
+
+    variants = {
+        "fp64_atomic": fea.make_operator(kind=1, precision=0, scatter=0, poisson=0.3),
+        "fp32_atomic": fea.make_operator(kind=1, precision=1, scatter=0, poisson=0.3),
+    }
+    head = args.variant
+    results = {}
+    for name in ([head] + [v for v in variants if v != head]):
+        op = variants[name]
+        nk = fea.fea_assemble_launches(op, sysm.handle)
+        steps = args.steps if name == head else max(3, min(args.steps, 5))
+        # one set of profiling events per timed step: events[1] -> events[-1] brackets the kernels
+        ev_steps = [[torch.cuda.Event(enable_timing=True) for _ in range(2 + nk)] for _ in range(steps)]
+        for evs in ev_steps:
+            for e in evs:
+                e.record()
+        fea.set_events(op, None)
+        for _ in range(args.warmup):
+            sysm.assemble(op)
+        sysm.check()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank) if name == head else None
+        if clocks:
+            clocks.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for k in range(steps):
+            fea.set_events(op, ev_steps[k])
+            sysm.assemble(op)
+        end.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        if dist is not None:
+            dist.barrier()
+        total_ms = start.elapsed_time(end)
+        kern_ms = [evs[1].elapsed_time(evs[-1]) for evs in ev_steps]
+        fea.set_events(op, None)
+        sysm.check()
+        if dist is not None:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        results[name] = dict(ms_per_step=total_ms / steps, kernel_ms=sum(kern_ms) / len(kern_ms),
+                             launches=nk, steps=steps, clocks=clk)
+
+    # end to end through the C-ABI with host buffers: H2D of the step input (node
+    # coordinates, pinned), assemble, D2H of the result (A and b, pinned)
+    op = variants[head]
+    fea.set_events(op, None)
+    coords_h = torch.from_numpy(mesh.coords.reshape(-1)).pin_memory()
+    coords_d = torch.empty_like(coords_h, device=dev)
+    A_h = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    b_h = torch.empty(sysm.b.numel(), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(2):
+        coords_d.copy_(coords_h, non_blocking=True)
+        fea.fea_mesh_set_coords(sysm.handle, coords_d)
+        sysm.assemble(op)
+        A_h.copy_(sysm.A, non_blocking=True)
+        b_h.copy_(sysm.b, non_blocking=True)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(e2e_steps):
+        coords_d.copy_(coords_h, non_blocking=True)
+        fea.fea_mesh_set_coords(sysm.handle, coords_d)
+        sysm.assemble(op)
+        A_h.copy_(sysm.A, non_blocking=True)
+        b_h.copy_(sysm.b, non_blocking=True)
+    s1.record()
+    torch.cuda.synchronize()
+    e2e_ms = s0.elapsed_time(s1) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    sysm.check()
+
+    if rank == 0:
+        r = results[head]
+        hbm, peak_kind = _peaks()
+        by = algorithmic_bytes(N, E, nnz)
+        achieved = by / (r["kernel_ms"] * 1e-3) / 1e9
+        fl = algorithmic_flops_hex_elasticity(E)
+        line = {
+            "metric": METRIC,
+            "value": world * E / (r["ms_per_step"] * 1e-3),
+            "unit": "elements/s",
+            "n_gpus": world,
+            "steps": r["steps"],
+            "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 integrate + f64 accumulate" if "fp32" in head else "f64",
+            "data": "synthetic (seeded jittered hex8 cube; the paper's meshes are not available)",
+            "config": {"workload": "hex8 linear elasticity, 128^3 jittered cube (+-0.2h, PCG64 seed 2), "
+                                   "2,097,152 elements, 513,599,625 nonzeros, 2x2x2 Gauss",
+                       "variant": head, "l2": "inputs larger than L2 (A alone is 4.1 GB)",
+                       "parallelism": f"replicas x{world} (partial-row, no exchange)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": peak_kind,
+                         "algorithmic_bytes": by, "kernel_ms": r["kernel_ms"],
+                         "fp32_tflops_needed": fl / (r["kernel_ms"] * 1e-3) / 1e12},
+            "comparator": {"variant": "fp64_atomic",
+                           "value": world * E / (results["fp64_atomic"]["ms_per_step"] * 1e-3),
+                           "ms_per_step": results["fp64_atomic"]["ms_per_step"],
+                           "kernel_ms": results["fp64_atomic"]["kernel_ms"]},
+            "variants": {k: {"ms_per_step": v["ms_per_step"], "kernel_ms": v["kernel_ms"],
+                             "elements_per_s": E / (v["ms_per_step"] * 1e-3)} for k, v in results.items()},
+            "pattern_build_s": pattern_s,
+            "clocks": r["clocks"],
+            "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s",
+                    "h2d_bytes_per_step": int(coords_h.numel() * 8),
+                    "d2h_bytes_per_step": int((A_h.numel() + b_h.numel()) * 8)},
+            "gpu_launches": r["launches"] * r["steps"],
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def _slab(mesh, layers, n):
+    """The first `layers` cell layers (z) of the hex cube: a bounded sample of the workload."""
+    from paper_1805_03949_gb300 import meshgen as mg
+    E = layers * n * n
+    nodes_used = (layers + 1) * (n + 1) ** 2
+    return mg.Mesh(mesh.coords[:nodes_used].copy(), mesh.types[:E].copy(), mesh.conn_offsets[:E + 1].copy(),
+                   mesh.conn[:8 * E].copy(), {"kind": "slab", "layers": layers})
+
+
+def cpu_baseline(args, mesh=None, layers=None):
+    from oracle import oracle as O
+    n = args.n
+    mesh = mesh if mesh is not None else c2_mesh(n)
+    layers = layers or args.cpu_layers
+    sub = _slab(mesh, layers, n)
+    pat = O.pattern(sub, 3)
+    t0 = time.perf_counter()
+    O.assemble(sub, O.OP_ELASTICITY, pat=pat, young=1.0, poisson=0.3)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n_elems / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {layers} of 128 cell layers of the workload ({sub.n_elems} elements), "
+                      f"single-thread FP64 oracle, element-index order, pattern excluded",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    mesh = c2_mesh(args.n)
+    vals, secs = [], []
+    for _ in range(args.warmup):
+        cpu_baseline(args, mesh, layers=1)
+    for _ in range(args.steps):
+        cb = cpu_baseline(args, mesh, layers=args.ref_layers)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    E = args.ref_layers * args.n * args.n
+    ms = 1e3 * statistics.median(secs)
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "hex8 linear elasticity, 128^3 jittered cube (+-0.2h, PCG64 seed 2), "
+                                   "2,097,152 elements, 513,599,625 nonzeros, 2x2x2 Gauss",
+                       "sample": f"{args.ref_layers} cell layers ({E} elements) per step"},
+            "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_layers} of 128 cell layers per step"},
+            "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="fp32_atomic")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--cpu-layers", type=int, default=8)
+    ap.add_argument("--ref-layers", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * fea_gb300.h -- C-ABI of the GB300 (sm_103a) finite element assembly engine.
+ *
+ * The engine runs the element loop of the MPI+X assembly paper (Alg.
+ * "sequential assembly", Sec. 2.1.1): for every element e it computes the
+ * element matrix A^e and right-hand side b^e by Gauss quadrature and
+ * scatter-adds them into one CSR system, A += P_e^T A^e P_e, b += P_e^T b^e.
+ * The system is the square "partial-row" local matrix of Sec. 3.1: every
+ * node the mesh holds has its own rows, and the matrix is assembled from the
+ * elements of this mesh only.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: FEA_OK (0) or a negative
+ *    fea_status code; fea_last_error() then returns a message (thread-local).
+ *  - Pointers named *_d are DEVICE pointers (cudaMalloc or torch tensors on
+ *    the current device); the caller owns them and the library never frees or
+ *    keeps them beyond the call.  Pointers named *_h are host pointers.
+ *  - Every call that launches work takes a cudaStream_t (passed as void*,
+ *    NULL = legacy default stream) and is stream-ordered; it returns as soon
+ *    as the work is enqueued.  Calls documented as "synchronous" wait for the
+ *    stream.
+ *  - Errors found on the device (an inverted element, a row wider than the
+ *    builder supports) are latched in a per-mesh status word and reported by
+ *    the next synchronous call on that mesh or by fea_check().
+ *  - A mesh handle is library-owned device memory; it is used by one stream
+ *    at a time (calls on the same handle from two streams must be ordered by
+ *    the caller).
+ *
+ * Element types and local node order (the reference elements):
+ *  FEA_TET4   simplex, nodes (0,0,0) (1,0,0) (0,1,0) (0,0,1)
+ *  FEA_PYR5   base [-1,1]^2 at zeta=0 counter-clockwise seen from the apex,
+ *             then the apex (0,0,1); rational basis
+ *  FEA_PRISM6 triangle (0,0) (1,0) (0,1) at zeta=-1, then the same at +1
+ *  FEA_HEX8   [-1,1]^3, (000,100,110,010,001,101,111,011)
+ * Jacobian J_ij = dx_i/dxi_j must have det J > 0 at every quadrature point.
+ */
+#ifndef FEA_GB300_H
+#define FEA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEA_ABI_VERSION 1
+
+typedef enum {
+  FEA_OK = 0,
+  FEA_ERR_ARG = -1,              /* invalid argument (checked on the host)       */
+  FEA_ERR_OOM = -2,              /* a library allocation failed                  */
+  FEA_ERR_CUDA = -3,             /* a CUDA runtime call failed                   */
+  FEA_ERR_INVERTED_ELEMENT = -4, /* det J <= 0 at a quadrature point             */
+  FEA_ERR_NO_CONVERGENCE = -5,   /* a local Newton iteration did not converge    */
+  FEA_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up           */
+  FEA_ERR_INDEX_OVERFLOW = -7,   /* a count does not fit the index type          */
+  FEA_ERR_UNSUPPORTED = -8       /* valid input beyond a documented limit        */
+} fea_status;
+
+typedef enum { FEA_TET4 = 0, FEA_PYR5 = 1, FEA_PRISM6 = 2, FEA_HEX8 = 3 } fea_elem_type;
+
+typedef enum {
+  FEA_OP_DIFFUSION = 0,  /* scalar, 1 dof/node: A_ab = int k(x) grad N_a . grad N_b, b_a = int f N_a */
+  FEA_OP_ELASTICITY = 1  /* 3 dofs/node, isotropic small strain: A = int B^T D B, b = int f N        */
+} fea_op_kind;
+
+typedef enum {
+  FEA_FP64 = 0,          /* geometry, integration and accumulation in FP64 */
+  FEA_FP32_INTEGRATE = 1 /* element integration in FP32, accumulation into A and b in FP64;
+                            Jacobian, determinant and inverse in FP64 for distorted elements
+                            (Frobenius condition number of J above FEA_KAPPA_FP64 at some
+                            quadrature point, or det J near zero), FP32 otherwise */
+} fea_precision;
+
+#define FEA_KAPPA_FP64 12.0
+
+typedef enum {
+  FEA_SCATTER_ATOMIC = 0, /* FP64 atomic adds into A and b (the paper's Alg. "no coloring") */
+  FEA_SCATTER_COLOR = 1,  /* element coloring, plain read-modify-write per color (Alg. "coloring") */
+  FEA_SCATTER_BLOCK = 2   /* locality blocks accumulated in shared memory, block-boundary
+                             entries resolved globally (Alg. "local partitioning" / "multideps") */
+} fea_scatter;
+
+/* Mesh description for fea_mesh_upload.  coords is xyz per node (AoS,
+ * float64 [3*n_nodes]); element e has type types[e] and nodes
+ * conn[conn_offsets[e] .. conn_offsets[e+1]) in the local order above.
+ * on_device = 0: the five arrays are host pointers; 1: device pointers. */
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_elems;
+  const double* coords;
+  const uint8_t* types;
+  const int64_t* conn_offsets;
+  const int32_t* conn;
+  int32_t on_device;
+  int32_t reserved;
+} fea_mesh_desc;
+
+/* The operator to assemble.
+ *  kind       fea_op_kind
+ *  precision  fea_precision
+ *  scatter    fea_scatter
+ *  tet_rule   0: tet4 uses the 1-point centroid rule, 1: the 4-point degree-2 rule.
+ *             pyr5 always uses 8 points (2x2 Gauss x 2-point Gauss-Jacobi on the
+ *             collapsed cube), prism6 6 points (3-point triangle x 2-point Gauss),
+ *             hex8 2x2x2 Gauss.
+ *  diffusion  k(x) = k0 + k2 * x^2 (x = physical x-coordinate), source f
+ *  elasticity young, poisson, body_force[3]
+ *  events     optional profiling hook (NULL to skip): cudaEvent_t handles the
+ *             call records on its stream -- events[0] before zeroing A and b,
+ *             events[1] after zeroing, events[2 + j] after the j-th kernel it
+ *             launches (only those with index < n_events are recorded).
+ */
+typedef struct {
+  int32_t kind;
+  int32_t precision;
+  int32_t scatter;
+  int32_t tet_rule;
+  double k0, k2, source;
+  double young, poisson;
+  double body_force[3];
+  void** events;
+  int32_t n_events;
+  int32_t reserved;
+} fea_operator;
+
+typedef struct fea_mesh fea_mesh;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* fea_last_error(void);
+
+/* FEA_ABI_VERSION of the loaded library. */
+int fea_abi_version(void);
+
+/* Copy a mesh to the device and prepare it (a1 of the element loop: element
+ * lists per type in input order, packed per-type connectivity, offsets of the
+ * element-to-nonzero map).  Checks on the host that every type is known, that
+ * conn_offsets matches the node count of each type and that node ids are in
+ * range (host input), or on the device (device input; then synchronous).
+ * n_nodes < 2^31, n_elems < 2^31.  *out receives the handle.
+ * Synchronous. */
+int fea_mesh_upload(const fea_mesh_desc* desc, void* stream, fea_mesh** out);
+
+/* Replace the node coordinates of a mesh (moving meshes, Newton updates):
+ * coords is float64 [3*n_nodes], a device pointer if on_device else a host
+ * pointer.  Stream-ordered (a pageable host source is copied before return). */
+int fea_mesh_set_coords(fea_mesh* mesh, const double* coords, int on_device, void* stream);
+
+/* Free a handle and every device buffer it owns (synchronizes the device). */
+int fea_mesh_destroy(fea_mesh* mesh);
+
+/* Sizes: nodes, elements, and map_len = sum over elements of n_e^2 (the
+ * length of node_map).  Host call, no device work. */
+int fea_mesh_info(const fea_mesh* mesh, int64_t* n_nodes, int64_t* n_elems, int64_t* map_len);
+
+/* Build the node graph of the mesh inside the handle (Sec. 3.1: nodes i and j
+ * couple iff some element holds both, diagonal included; rows sorted
+ * ascending) and return the number of scalar nonzeros for ndof interleaved
+ * dofs per node: *nnz = ndof^2 * (node nonzeros).  ndof in {1, 3}.
+ * Synchronous (the count is read back).  FEA_ERR_UNSUPPORTED if a node
+ * gathers more than 1024 (element, node) incidences. */
+int fea_pattern_size(fea_mesh* mesh, int ndof, int64_t* nnz, void* stream);
+
+/* Write the scalar CSR pattern and the element-to-nonzero map (needs a
+ * preceding fea_pattern_size with the same ndof).
+ *  row_ptr_d  int64 [n_nodes*ndof + 1]  row d*i+c starts at row_ptr_d[d*i+c]
+ *  col_idx_d  int32 [nnz]               row d*i+c holds columns d*j+c' for the
+ *                                       node neighbours j ascending, c' = 0..d-1
+ *  node_map_d int32 [map_len]           node_map_d[off(e) + a*n_e + b] = k, the
+ *                                       rank of node conn[e][b] among the sorted
+ *                                       neighbours of node conn[e][a]; off(e) =
+ *                                       sum_{e'<e} n_{e'}^2 over ORIGINAL ids.
+ *                                       Entry (d*i+c, d*j+c') of A sits at
+ *                                       row_ptr_d[d*i+c] + d*k + c'.
+ * col_idx_d or node_map_d may be NULL to skip them.  Stream-ordered.
+ * Positions are int64 (row_ptr), columns int32: ndof*n_nodes must be < 2^31
+ * (checked by fea_pattern_size, FEA_ERR_INDEX_OVERFLOW). */
+int fea_build_csr_pattern(fea_mesh* mesh, int ndof, int64_t* row_ptr_d, int32_t* col_idx_d,
+                          int32_t* node_map_d, void* stream);
+
+/* Assemble (Alg. "sequential assembly", parallelised per fea_scatter):
+ * OVERWRITES A_vals_d (float64 [nnz]) and b_d (float64 [n_nodes*ndof]) with
+ * sum_e P_e^T A^e P_e and sum_e P_e^T b^e, using the pattern and map written
+ * by fea_build_csr_pattern for ndof = 1 (diffusion) or 3 (elasticity).
+ * Stream-ordered; an inverted element is latched in the mesh status and
+ * reported by fea_check (the values are then unspecified). */
+int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d,
+                 const int32_t* node_map_d, double* A_vals_d, double* b_d, void* stream);
+
+/* Number of kernels one fea_assemble call with this operator launches on this
+ * mesh (after its pattern is built).  Host call. */
+int fea_assemble_launches(const fea_operator* op, const fea_mesh* mesh, int* n_kernels);
+
+/* Wait for the stream and return the mesh's latched device status (and clear
+ * it).  FEA_ERR_INVERTED_ELEMENT names the first element id found in the
+ * message.  Synchronous. */
+int fea_check(fea_mesh* mesh, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEA_GB300_H */

@@ -195,10 +195,16 @@ int oracle_shape(int type, const double* p, double* N, double* dN) {
 /* ---------------------------------------------------------------------------
  * Element matrix.  params: diffusion {k0, k2, f}; elasticity {E, nu, fx, fy, fz}.
  * Ae is (nn*d) x (nn*d) row-major with index a*d+c, be has nn*d entries, Se/Sb
- * the magnitude sums.  Returns 0, or 1 if detJ <= 0 at some quadrature point.
+ * the componentwise magnitude sums.  Ne (may be NULL) receives the normwise
+ * scale of each entry: the Cauchy-Schwarz bound of every quadrature term,
+ * |w detJ| |k| |g_a| |g_b| (diffusion) or |w detJ| (|lam| + 2|mu|) |g_a| |g_b|
+ * (elasticity), with g_a = grad N_a and |.| the Euclidean norm.  A rounding of
+ * the gradients by a relative amount eps (normwise) moves an entry by at most
+ * about eps times its normwise scale.
+ * Returns 0, or 1 if detJ <= 0 at some quadrature point.
  * ------------------------------------------------------------------------- */
 int oracle_element(int type, int tet_rule, int op, const double* params, const double* X,
-                   double* Ae, double* be, double* Se, double* Sb) {
+                   double* Ae, double* be, double* Se, double* Sb, double* Ne) {
   int nn = or_nodes(type);
   int d = (op == OR_OP_DIFFUSION) ? 1 : 3;
   int n = nn * d;
@@ -208,13 +214,15 @@ int oracle_element(int type, int tet_rule, int op, const double* params, const d
   memset(be, 0, sizeof(double) * n);
   memset(Se, 0, sizeof(double) * n * n);
   memset(Sb, 0, sizeof(double) * n);
+  if (Ne) memset(Ne, 0, sizeof(double) * n * n);
 
   double D[6][6];
+  double lam = 0.0, mu = 0.0;
   memset(D, 0, sizeof(D));
   if (op == OR_OP_ELASTICITY) {
     double E = params[0], nu = params[1];
-    double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    double mu = E / (2.0 * (1.0 + nu));
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    mu = E / (2.0 * (1.0 + nu));
     for (int i = 0; i < 3; ++i) {
       for (int j = 0; j < 3; ++j) D[i][j] = lam;
       D[i][i] = lam + 2.0 * mu;
@@ -257,6 +265,8 @@ int oracle_element(int type, int tet_rule, int op, const double* params, const d
         for (int j = 0; j < 3; ++j) G[a][i] += dN[a][j] * Jinv[j][i];
       }
     double wd = w[q] * det;
+    double gnorm[OR_MAXN];
+    for (int a = 0; a < nn; ++a) gnorm[a] = sqrt(G[a][0] * G[a][0] + G[a][1] * G[a][1] + G[a][2] * G[a][2]);
 
     if (op == OR_OP_DIFFUSION) {
       double k0 = params[0], k2 = params[1], f = params[2];
@@ -268,6 +278,7 @@ int oracle_element(int type, int tet_rule, int op, const double* params, const d
           for (int i = 0; i < 3; ++i) { s += G[a][i] * G[b][i]; sa += fabs(G[a][i] * G[b][i]); }
           Ae[a * n + b] += wd * k * s;
           Se[a * n + b] += fabs(wd) * kabs * sa;
+          if (Ne) Ne[a * n + b] += fabs(wd) * kabs * gnorm[a] * gnorm[b];
         }
         be[a] += wd * f * N[a];
         Sb[a] += fabs(wd) * fabs(f) * fabs(N[a]);
@@ -297,6 +308,8 @@ int oracle_element(int type, int tet_rule, int op, const double* params, const d
                 }
               Ae[(a * 3 + c) * n + b * 3 + cc] += wd * s;
               Se[(a * 3 + c) * n + b * 3 + cc] += fabs(wd) * sa;
+              if (Ne)
+                Ne[(a * 3 + c) * n + b * 3 + cc] += fabs(wd) * (fabs(lam) + 2.0 * fabs(mu)) * gnorm[a] * gnorm[b];
             }
       for (int a = 0; a < nn; ++a)
         for (int c = 0; c < 3; ++c) {
@@ -323,6 +336,7 @@ static int cmp_i32(const void* a, const void* b) {
 
 int64_t oracle_pattern(int64_t n_nodes, int64_t n_elems, const uint8_t* types, const int64_t* conn_off,
                        const int32_t* conn, int64_t* row_ptr, int32_t* col_idx, int32_t* node_map) {
+  if (n_nodes <= 0 || n_elems < 0) return -1;
   /* node -> incident elements */
   int64_t* cnt = (int64_t*)calloc((size_t)n_nodes + 1, sizeof(int64_t));
   for (int64_t e = 0; e < n_elems; ++e) {
@@ -404,18 +418,18 @@ void oracle_expand_pattern(int64_t n_nodes, int d, const int64_t* rp, const int3
 int64_t oracle_assemble(int64_t n_nodes, int64_t n_elems, const uint8_t* types, const int64_t* conn_off,
                         const int32_t* conn, const double* coords, int op, int tet_rule,
                         const double* params, const int64_t* rp_s, const int32_t* node_map,
-                        double* A, double* b, double* SA, double* Sb) {
+                        double* A, double* b, double* SA, double* Sb, double* NA) {
   int d = (op == OR_OP_DIFFUSION) ? 1 : 3;
   (void)n_nodes;
   double X[3 * OR_MAXN];
-  double Ae[24 * 24], be[24], Se[24 * 24], Sbe[24];
+  double Ae[24 * 24], be[24], Se[24 * 24], Sbe[24], Ne[24 * 24];
   int64_t off = 0;
   for (int64_t e = 0; e < n_elems; ++e) {
     int ne = (int)(conn_off[e + 1] - conn_off[e]);
     const int32_t* en = conn + conn_off[e];
     for (int a = 0; a < ne; ++a)
       for (int i = 0; i < 3; ++i) X[3 * a + i] = coords[3 * (int64_t)en[a] + i];
-    if (oracle_element(types[e], tet_rule, op, params, X, Ae, be, Se, Sbe)) return -(e + 1);
+    if (oracle_element(types[e], tet_rule, op, params, X, Ae, be, Se, Sbe, Ne)) return -(e + 1);
     int n = ne * d;
     for (int a = 0; a < ne; ++a)
       for (int c = 0; c < d; ++c) {
@@ -426,6 +440,7 @@ int64_t oracle_assemble(int64_t n_nodes, int64_t n_elems, const uint8_t* types, 
             int64_t pos = rp_s[row] + d * k + cc;
             A[pos] += Ae[(a * d + c) * n + bb * d + cc];
             if (SA) SA[pos] += Se[(a * d + c) * n + bb * d + cc];
+            if (NA) NA[pos] += Ne[(a * d + c) * n + bb * d + cc];
           }
         }
         b[row] += be[a * d + c];
@@ -450,7 +465,7 @@ int64_t oracle_assemble_rows(int64_t n_nodes, int64_t n_elems, const uint8_t* ty
                              const int32_t* conn, const double* coords, int op, int tet_rule,
                              const double* params, int64_t n_req, const int32_t* req_nodes, int64_t max_cols,
                              int32_t* cols_out, int64_t* deg_out, double* vals, double* svals,
-                             double* bvals, double* sbvals) {
+                             double* bvals, double* sbvals, double* nvals) {
   int d = (op == OR_OP_DIFFUSION) ? 1 : 3;
   int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_nodes);
   for (int64_t i = 0; i < n_nodes; ++i) slot[i] = -1;
@@ -483,10 +498,11 @@ int64_t oracle_assemble_rows(int64_t n_nodes, int64_t n_elems, const uint8_t* ty
   }
   memset(vals, 0, sizeof(double) * (size_t)(n_req * max_cols * d * d));
   memset(svals, 0, sizeof(double) * (size_t)(n_req * max_cols * d * d));
+  memset(nvals, 0, sizeof(double) * (size_t)(n_req * max_cols * d * d));
   memset(bvals, 0, sizeof(double) * (size_t)(n_req * d));
   memset(sbvals, 0, sizeof(double) * (size_t)(n_req * d));
   double X[3 * OR_MAXN];
-  double Ae[24 * 24], be[24], Se[24 * 24], Sbe[24];
+  double Ae[24 * 24], be[24], Se[24 * 24], Sbe[24], Ne[24 * 24];
   for (int64_t e = 0; e < n_elems; ++e) {
     int ne = (int)(conn_off[e + 1] - conn_off[e]);
     const int32_t* en = conn + conn_off[e];
@@ -495,7 +511,7 @@ int64_t oracle_assemble_rows(int64_t n_nodes, int64_t n_elems, const uint8_t* ty
     if (!hit) continue;
     for (int a = 0; a < ne; ++a)
       for (int i = 0; i < 3; ++i) X[3 * a + i] = coords[3 * (int64_t)en[a] + i];
-    if (oracle_element(types[e], tet_rule, op, params, X, Ae, be, Se, Sbe)) {
+    if (oracle_element(types[e], tet_rule, op, params, X, Ae, be, Se, Sbe, Ne)) {
       free(slot); free(tmp); free(tcount); return -(e + 1);
     }
     int n = ne * d;
@@ -511,6 +527,7 @@ int64_t oracle_assemble_rows(int64_t n_nodes, int64_t n_elems, const uint8_t* ty
             int64_t pos = r * max_cols * d * d + c * (deg_out[r] * d) + d * k + cc;
             vals[pos] += Ae[(a * d + c) * n + bb * d + cc];
             svals[pos] += Se[(a * d + c) * n + bb * d + cc];
+            nvals[pos] += Ne[(a * d + c) * n + bb * d + cc];
           }
       }
       for (int c = 0; c < d; ++c) {

@@ -57,12 +57,12 @@ def lib():
             _lib.oracle_expand_pattern.restype = None
             _lib.oracle_expand_pattern.argtypes = [_i64, _i32, _p, _p, _p, _p]
             _lib.oracle_assemble.restype = _i64
-            _lib.oracle_assemble.argtypes = [_i64, _i64, _p, _p, _p, _p, _i32, _i32, _p, _p, _p, _p, _p, _p, _p]
+            _lib.oracle_assemble.argtypes = [_i64, _i64, _p, _p, _p, _p, _i32, _i32, _p, _p, _p, _p, _p, _p, _p, _p]
             _lib.oracle_assemble_rows.restype = _i64
             _lib.oracle_assemble_rows.argtypes = [_i64, _i64, _p, _p, _p, _p, _i32, _i32, _p, _i64, _p, _i64,
-                                                  _p, _p, _p, _p, _p, _p]
+                                                  _p, _p, _p, _p, _p, _p, _p]
             _lib.oracle_element.restype = _i32
-            _lib.oracle_element.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p]
+            _lib.oracle_element.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p, _p]
             _lib.oracle_quadrature.restype = _i32
             _lib.oracle_quadrature.argtypes = [_i32, _i32, _p, _p]
             _lib.oracle_shape.restype = _i32
@@ -117,11 +117,14 @@ def element(etype: int, X, op: int = OP_DIFFUSION, tet_rule: int = 1, **kw):
     X = _c(X, np.float64)
     d = 1 if op == OP_DIFFUSION else 3
     n = NODES[etype] * d
-    Ae = np.zeros((n, n)); be = np.zeros(n); Se = np.zeros((n, n)); Sb = np.zeros(n)
+    Ae = np.zeros((n, n)); be = np.zeros(n); Se = np.zeros((n, n)); Sb = np.zeros(n); Ne = np.zeros((n, n))
     params = op_params(op, **kw)
-    rc = lib().oracle_element(etype, tet_rule, op, _ptr(params), _ptr(X), _ptr(Ae), _ptr(be), _ptr(Se), _ptr(Sb))
+    rc = lib().oracle_element(etype, tet_rule, op, _ptr(params), _ptr(X), _ptr(Ae), _ptr(be), _ptr(Se), _ptr(Sb),
+                              _ptr(Ne))
     if rc:
         raise InvertedElement(-1)
+    if kw.get("with_norm"):
+        return Ae, be, Se, Sb, Ne
     return Ae, be, Se, Sb
 
 
@@ -155,23 +158,24 @@ def pattern(mesh, ndof: int = 1):
 def assemble(mesh, op: int = OP_DIFFUSION, tet_rule: int = 1, pat=None, **kw):
     """Assemble A (CSR values) and b in element-index order, with magnitude sums.
 
-    Returns dict(row_ptr, col_idx, node_map, A, b, SA, Sb).
+    Returns dict(row_ptr, col_idx, node_map, A, b, SA, Sb, NA): SA/Sb the
+    componentwise magnitude sums, NA the normwise scale (Nb = Sb).
     """
     d = 1 if op == OP_DIFFUSION else 3
     if pat is None:
         pat = pattern(mesh, d)
     rps, cols, nmap = pat
-    A = np.zeros(cols.shape[0]); SA = np.zeros_like(A)
+    A = np.zeros(cols.shape[0]); SA = np.zeros_like(A); NA = np.zeros_like(A)
     b = np.zeros(mesh.n_nodes * d); Sb = np.zeros_like(b)
     params = op_params(op, **kw)
     types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
     coords = _c(mesh.coords, np.float64)
     rc = lib().oracle_assemble(mesh.n_nodes, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords),
                                op, tet_rule, _ptr(params), _ptr(rps), _ptr(nmap),
-                               _ptr(A), _ptr(b), _ptr(SA), _ptr(Sb))
+                               _ptr(A), _ptr(b), _ptr(SA), _ptr(Sb), _ptr(NA))
     if rc < 0:
         raise InvertedElement(-rc - 1)
-    return dict(row_ptr=rps, col_idx=cols, node_map=nmap, A=A, b=b, SA=SA, Sb=Sb)
+    return dict(row_ptr=rps, col_idx=cols, node_map=nmap, A=A, b=b, SA=SA, Sb=Sb, NA=NA, Nb=Sb)
 
 
 def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_cols: int = 512, **kw):
@@ -185,14 +189,14 @@ def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_co
     r = len(req)
     cols = np.zeros((r, max_cols), dtype=np.int32)
     deg = np.zeros(r, dtype=np.int64)
-    vals = np.zeros(r * max_cols * d * d); svals = np.zeros_like(vals)
+    vals = np.zeros(r * max_cols * d * d); svals = np.zeros_like(vals); nvals = np.zeros_like(vals)
     bv = np.zeros(r * d); sbv = np.zeros_like(bv)
     params = op_params(op, **kw)
     types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
     coords = _c(mesh.coords, np.float64)
     rc = lib().oracle_assemble_rows(mesh.n_nodes, mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords),
                                     op, tet_rule, _ptr(params), r, _ptr(req), max_cols, _ptr(cols), _ptr(deg),
-                                    _ptr(vals), _ptr(svals), _ptr(bv), _ptr(sbv))
+                                    _ptr(vals), _ptr(svals), _ptr(bv), _ptr(sbv), _ptr(nvals))
     if rc == -1:
         raise ValueError("row wider than max_cols")
     if rc < 0:
@@ -204,6 +208,7 @@ def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_co
         out.append(dict(cols=cols[t, :k].copy(),
                         vals=vals[base:base + d * k * d].reshape(d, k * d).copy(),
                         svals=svals[base:base + d * k * d].reshape(d, k * d).copy(),
+                        nvals=nvals[base:base + d * k * d].reshape(d, k * d).copy(),
                         b=bv[t * d:(t + 1) * d].copy(), sb=sbv[t * d:(t + 1) * d].copy()))
     return out
 

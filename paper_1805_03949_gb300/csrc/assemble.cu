@@ -1,0 +1,570 @@
+// assemble.cu -- batched element integration and race-free scatter into CSR.
+//
+// The element loop of the MPI+X assembly paper (Alg. "sequential
+// assembly", Sec. 2.1.1) on the GPU: every CTA integrates a tile of elements
+// of one type and adds the element matrices into A and b.  The race on the
+// shared entries (Sec. 3.2.1) is treated by the variant of fea_scatter:
+//   ATOMIC  FP64 atomic adds, the GPU form of Alg. "no coloring".
+//
+// Tile schedule of one CTA (128 threads, EPC elements):
+//   phase 0  gather the node coordinates of the tile into shared memory
+//   phase 1  one thread per (element, quadrature point): Jacobian, det, J^{-1},
+//            physical gradients g_a and the weight w*detJ (FP64, or FP32 with
+//            an FP64 redo of distorted elements)
+//   phase 2  LPE = n_e * SPLIT lanes per element: lane (a, half) accumulates
+//            the row block A^e_(a, b) for its NB columns b over the points
+//   phase 3  the same lane scatters its row block through the rank map.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "element.cuh"
+#include "fea_internal.cuh"
+
+namespace fea {
+
+// ---------------------------------------------------------------------------
+// host: reference tables
+// ---------------------------------------------------------------------------
+static void ref_shape(int type, const double p[3], double N[8], double dN[8][3]) {
+  const double x = p[0], y = p[1], z = p[2];
+  for (int a = 0; a < 8; ++a) N[a] = dN[a][0] = dN[a][1] = dN[a][2] = 0.0;
+  switch (type) {
+    case FEA_TET4: {
+      N[0] = 1.0 - x - y - z;
+      N[1] = x;
+      N[2] = y;
+      N[3] = z;
+      for (int j = 0; j < 3; ++j) {
+        dN[0][j] = -1.0;
+        dN[j + 1][j] = 1.0;
+      }
+      break;
+    }
+    case FEA_HEX8: {
+      // corner signs in (000,100,110,010,001,101,111,011) order
+      for (int a = 0; a < 8; ++a) {
+        const int bx = ((a + 1) >> 1) & 1, by = (a >> 1) & 1, bz = a >> 2;
+        const double sx = bx ? 1.0 : -1.0, sy = by ? 1.0 : -1.0, sz = bz ? 1.0 : -1.0;
+        const double fx = 0.5 * (1.0 + sx * x), fy = 0.5 * (1.0 + sy * y), fz = 0.5 * (1.0 + sz * z);
+        N[a] = fx * fy * fz;
+        dN[a][0] = 0.5 * sx * fy * fz;
+        dN[a][1] = 0.5 * sy * fx * fz;
+        dN[a][2] = 0.5 * sz * fx * fy;
+      }
+      break;
+    }
+    case FEA_PRISM6: {
+      const double L[3] = {1.0 - x - y, x, y};
+      const double Lx[3] = {-1.0, 1.0, 0.0}, Ly[3] = {-1.0, 0.0, 1.0};
+      for (int s = 0; s < 2; ++s) {
+        const double h = 0.5 * (1.0 + (s ? z : -z)), hz = s ? 0.5 : -0.5;
+        for (int i = 0; i < 3; ++i) {
+          N[3 * s + i] = L[i] * h;
+          dN[3 * s + i][0] = Lx[i] * h;
+          dN[3 * s + i][1] = Ly[i] * h;
+          dN[3 * s + i][2] = L[i] * hz;
+        }
+      }
+      break;
+    }
+    case FEA_PYR5: {
+      // base corner i: N = (1 - z + sx x)(1 - z + sy y) / (4 (1 - z)); apex: N = z
+      const double sx[4] = {-1.0, 1.0, 1.0, -1.0}, sy[4] = {-1.0, -1.0, 1.0, 1.0};
+      const double t = 1.0 - z;
+      for (int i = 0; i < 4; ++i) {
+        const double u = t + sx[i] * x, v = t + sy[i] * y;
+        N[i] = u * v / (4.0 * t);
+        dN[i][0] = sx[i] * v / (4.0 * t);
+        dN[i][1] = sy[i] * u / (4.0 * t);
+        // d/dz of u v / (4 t) with du/dz = dv/dz = -1, dt/dz = -1
+        dN[i][2] = (u * v - t * (u + v)) / (4.0 * t * t);
+      }
+      N[4] = z;
+      dN[4][2] = 1.0;
+      break;
+    }
+  }
+}
+
+static int ref_points(int slot, double P[8][3], double W[8]) {
+  const double g = 1.0 / std::sqrt(3.0);
+  const double gp[2] = {-g, g};
+  switch (slot) {
+    case kRuleTet1:
+      P[0][0] = P[0][1] = P[0][2] = 0.25;
+      W[0] = 1.0 / 6.0;
+      return 1;
+    case kRuleTet4: {
+      const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
+      for (int q = 0; q < 4; ++q) {
+        for (int j = 0; j < 3; ++j) P[q][j] = (q == j + 1) ? a : b;
+        W[q] = 1.0 / 24.0;
+      }
+      return 4;
+    }
+    case kRulePrism6: {
+      const double tri[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+      for (int q = 0; q < 6; ++q) {
+        P[q][0] = tri[q % 3][0];
+        P[q][1] = tri[q % 3][1];
+        P[q][2] = gp[q / 3];
+        W[q] = 1.0 / 6.0;
+      }
+      return 6;
+    }
+    case kRuleHex8:
+      for (int q = 0; q < 8; ++q) {
+        P[q][0] = gp[q & 1];
+        P[q][1] = gp[(q >> 1) & 1];
+        P[q][2] = gp[q >> 2];
+        W[q] = 1.0;
+      }
+      return 8;
+    default: {  // pyramid: collapsed cube, 2x2 Gauss x Gauss-Jacobi (weight (1-t)^2 on [0,1])
+      const double r = std::sqrt(10.0) / 15.0;
+      const double t[2] = {1.0 / 3.0 - r, 1.0 / 3.0 + r};
+      const double w2 = (1.0 / 12.0 - t[0] / 3.0) / (t[1] - t[0]);
+      const double wt[2] = {1.0 / 3.0 - w2, w2};
+      for (int q = 0; q < 8; ++q) {
+        const int k = q >> 2;
+        P[q][0] = gp[q & 1] * (1.0 - t[k]);
+        P[q][1] = gp[(q >> 1) & 1] * (1.0 - t[k]);
+        P[q][2] = t[k];
+        W[q] = wt[k];
+      }
+      return 8;
+    }
+  }
+}
+
+const RefRule& host_rule(int slot) {
+  static RefRule rules[kNumRules];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int s = 0; s < kNumRules; ++s) {
+      RefRule& R = rules[s];
+      std::memset(&R, 0, sizeof(R));
+      double P[8][3], W[8];
+      const int nq = ref_points(s, P, W);
+      for (int q = 0; q < nq; ++q) {
+        double N[8], dN[8][3];
+        ref_shape(rule_type(s), P[q], N, dN);
+        R.w[q] = W[q];
+        R.wf[q] = (float)W[q];
+        for (int a = 0; a < 8; ++a) {
+          R.N[q][a] = N[a];
+          R.Nf[q][a] = (float)N[a];
+          for (int j = 0; j < 3; ++j) {
+            R.dN[q][a][j] = dN[a][j];
+            R.dNf[q][a][j] = (float)dN[a][j];
+          }
+        }
+      }
+    }
+  });
+  return rules[slot];
+}
+
+// ---------------------------------------------------------------------------
+// device
+// ---------------------------------------------------------------------------
+struct AsmParams {
+  const double* coords;
+  const int32_t* tconn;     // [n][NN] packed connectivity of the group
+  const int32_t* ids;       // [n] original element ids (nullptr: identity)
+  const int64_t* mapoff;    // [n] node_map offsets (nullptr: id * NN^2)
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* node_map;
+  double* A;
+  double* b;
+  DevStatus* st;
+  double k0, k2, src;       // diffusion
+  double lam, mu;           // elasticity
+  double f[3];
+};
+
+template <int OP, int PREC, int NN, int NQ, int EPC>
+struct TileSmem {
+  using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
+  double X[EPC][NN][3];     // node coordinates
+  R G[EPC][NQ][NN][3];      // physical gradients
+  R S[EPC][NQ];             // w detJ k(x_q)
+  R W[EPC][NQ];             // w detJ
+  int flag[EPC];            // FP32 mode: element is distorted -> FP64 geometry
+};
+
+__device__ __forceinline__ void cofactors(const double J[3][3], double C[3][3]) {
+  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+}
+
+__device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {
+  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+}
+
+// FP64 geometry of point q of element le; results rounded to the tile type R.
+template <int OP, int NN, typename Smem>
+__device__ __forceinline__ void geometry_fp64(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
+                                              const AsmParams& P) {
+  using R = std::remove_reference_t<decltype(sm.G[0][0][0][0])>;
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double xq = sm.X[le][0][0];
+#pragma unroll
+  for (int a = 1; a < NN; ++a) {
+    const double d0 = sm.X[le][a][0] - sm.X[le][0][0];
+    const double d1 = sm.X[le][a][1] - sm.X[le][0][1];
+    const double d2 = sm.X[le][a][2] - sm.X[le][0][2];
+    xq += rr.N[q][a] * d0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      J[0][j] += d0 * rr.dN[q][a][j];
+      J[1][j] += d1 * rr.dN[q][a][j];
+      J[2][j] += d2 * rr.dN[q][a][j];
+    }
+  }
+  double C[3][3];
+  cofactors(J, C);
+  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
+  const double inv = 1.0 / det;
+#pragma unroll
+  for (int a = 0; a < NN; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      // g_a,i = sum_j dN_a/dxi_j (J^{-1})_{j i},  (J^{-1})_{j i} = C_{i j} / det
+      const double v = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+      sm.G[le][q][a][i] = (R)v;
+    }
+  }
+  const double wd = rr.w[q] * det;
+  sm.W[le][q] = (R)wd;
+  if constexpr (OP == FEA_OP_DIFFUSION)
+    sm.S[le][q] = (R)(wd * (P.k0 + P.k2 * xq * xq));
+  else
+    sm.S[le][q] = (R)wd;
+}
+
+// FP32 geometry on coordinates relative to node 0; returns false when the
+// element must take the FP64 path (distorted: Frobenius condition number of J
+// above FEA_KAPPA_FP64, or a determinant FP32 cannot trust).
+template <int OP, int NN, typename Smem>
+__device__ __forceinline__ bool geometry_fp32(Smem& sm, const RefRule& rr, int le, int q, const AsmParams& P) {
+  float J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  float xr = 0.0f;
+#pragma unroll
+  for (int a = 1; a < NN; ++a) {
+    const float d0 = (float)(sm.X[le][a][0] - sm.X[le][0][0]);
+    const float d1 = (float)(sm.X[le][a][1] - sm.X[le][0][1]);
+    const float d2 = (float)(sm.X[le][a][2] - sm.X[le][0][2]);
+    xr += rr.Nf[q][a] * d0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      J[0][j] += d0 * rr.dNf[q][a][j];
+      J[1][j] += d1 * rr.dNf[q][a][j];
+      J[2][j] += d2 * rr.dNf[q][a][j];
+    }
+  }
+  float C[3][3];
+  cofactors(J, C);
+  const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  float nj = 0.0f, nc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      nj += J[i][j] * J[i][j];
+      nc += C[i][j] * C[i][j];
+    }
+  // kappa_F^2 = |J|_F^2 |J^{-1}|_F^2 = |J|_F^2 |C|_F^2 / det^2
+  const float kappa2_max = (float)(FEA_KAPPA_FP64 * FEA_KAPPA_FP64);
+  if (!(det > 0.0f) || !(nj * nc <= kappa2_max * det * det)) return false;
+  const float inv = 1.0f / det;
+#pragma unroll
+  for (int a = 0; a < NN; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      sm.G[le][q][a][i] = (rr.dNf[q][a][0] * C[i][0] + rr.dNf[q][a][1] * C[i][1] + rr.dNf[q][a][2] * C[i][2]) * inv;
+  const float wd = rr.wf[q] * det;
+  sm.W[le][q] = wd;
+  if constexpr (OP == FEA_OP_DIFFUSION) {
+    const float x = (float)sm.X[le][0][0] + xr;
+    sm.S[le][q] = wd * ((float)P.k0 + (float)P.k2 * x * x);
+  } else {
+    sm.S[le][q] = wd;
+  }
+  return true;
+}
+
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+struct TileCfg {
+  static constexpr int NN = nodes_of(TYPE);
+  static constexpr int NQ = rule_nq(SLOT);
+  static constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
+  static constexpr int LPE = NN * SPLIT;        // lanes per element
+  static constexpr int EPW = 32 / LPE;          // elements per warp
+  static constexpr int WARPS = 4;
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int EPC = EPW * WARPS;       // elements per CTA
+  static constexpr int NB = NN / SPLIT;         // columns per lane
+  static_assert(NN % SPLIT == 0, "SPLIT must divide the node count");
+  using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
+  using Smem = TileSmem<OP, PREC, NN, NQ, EPC>;
+};
+
+// phases 0 and 1 for the tile of elements [e0, e0 + EPC)
+template <class Cfg, int OP, int PREC>
+__device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefRule& rr, const AsmParams& P,
+                                              int64_t e0) {
+  constexpr int NN = Cfg::NN, NQ = Cfg::NQ, EPC = Cfg::EPC;
+  for (int t = threadIdx.x; t < EPC * NN; t += Cfg::THREADS) {
+    const int le = t / NN, a = t % NN;
+    const int64_t et = e0 + le;
+    if (et < P.n) {
+      const int64_t node = P.tconn[et * NN + a];
+      sm.X[le][a][0] = P.coords[3 * node + 0];
+      sm.X[le][a][1] = P.coords[3 * node + 1];
+      sm.X[le][a][2] = P.coords[3 * node + 2];
+    }
+  }
+  if (threadIdx.x < EPC) sm.flag[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
+    const int le = t / NQ, q = t % NQ;
+    const int64_t et = e0 + le;
+    if (et >= P.n) continue;
+    if constexpr (PREC == FEA_FP64) {
+      geometry_fp64<OP, NN>(sm, rr, le, q, P.ids ? P.ids[et] : et, P);
+    } else {
+      if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
+    }
+  }
+  if constexpr (PREC != FEA_FP64) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
+      const int le = t / NQ, q = t % NQ;
+      const int64_t et = e0 + le;
+      if (et < P.n && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, P.ids ? P.ids[et] : et, P);
+    }
+  }
+  __syncthreads();
+}
+
+// phase 2: row block (a, columns b0 .. b0+NB) of element le, and its RHS
+template <class Cfg, int OP>
+__device__ __forceinline__ void row_block(const typename Cfg::Smem& sm, const RefRule& rr, const AsmParams& P,
+                                          int le, int a, int b0, typename Cfg::R (&K)[Cfg::NB][Cfg::D][Cfg::D],
+                                          typename Cfg::R (&rhs)[Cfg::D]) {
+  using R = typename Cfg::R;
+  constexpr int NB = Cfg::NB, D = Cfg::D, NQ = Cfg::NQ;
+#pragma unroll
+  for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int cc = 0; cc < D; ++cc) K[bb][c][cc] = R(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) rhs[c] = R(0);
+  const R lam = (R)P.lam, mu = (R)P.mu;
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    const R s = sm.S[le][q];
+    const R ga0 = sm.G[le][q][a][0], ga1 = sm.G[le][q][a][1], ga2 = sm.G[le][q][a][2];
+    if constexpr (OP == FEA_OP_DIFFUSION) {
+      const R sa0 = s * ga0, sa1 = s * ga1, sa2 = s * ga2;
+#pragma unroll
+      for (int bb = 0; bb < NB; ++bb) {
+        const R* gb = sm.G[le][q][b0 + bb];
+        K[bb][0][0] += sa0 * gb[0] + sa1 * gb[1] + sa2 * gb[2];
+      }
+    } else {
+      const R gl[3] = {s * lam * ga0, s * lam * ga1, s * lam * ga2};
+      const R gm[3] = {s * mu * ga0, s * mu * ga1, s * mu * ga2};
+#pragma unroll
+      for (int bb = 0; bb < NB; ++bb) {
+        const R gb[3] = {sm.G[le][q][b0 + bb][0], sm.G[le][q][b0 + bb][1], sm.G[le][q][b0 + bb][2]};
+        const R dot = gm[0] * gb[0] + gm[1] * gb[1] + gm[2] * gb[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) K[bb][c][cc] += gl[c] * gb[cc] + gm[cc] * gb[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) K[bb][c][c] += dot;
+      }
+    }
+    if (b0 == 0) {
+      R Nqa;
+      if constexpr (std::is_same<R, double>::value)
+        Nqa = rr.N[q][a];
+      else
+        Nqa = rr.Nf[q][a];
+      const R wN = sm.W[le][q] * Nqa;
+      if constexpr (OP == FEA_OP_DIFFUSION)
+        rhs[0] += wN * (R)P.src;
+      else
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rhs[c] += wN * (R)P.f[c];
+    }
+  }
+}
+
+// ATOMIC scatter: FP64 atomic adds of each row block (Alg. "no coloring")
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+__global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__ RefRule rr,
+                                                         const __grid_constant__ AsmParams P) {
+  using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
+  using R = typename Cfg::R;
+  constexpr int NN = Cfg::NN, D = Cfg::D, NB = Cfg::NB, LPE = Cfg::LPE, EPW = Cfg::EPW;
+  __shared__ typename Cfg::Smem sm;
+  const int64_t e0 = (int64_t)blockIdx.x * Cfg::EPC;
+  tile_geometry<Cfg, OP, PREC>(sm, rr, P, e0);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lw = lane / LPE;
+  if (lw >= EPW) return;
+  const int le = warp * EPW + lw;
+  const int64_t et = e0 + le;
+  if (et >= P.n) return;
+  const int r = lane % LPE;
+  const int a = r % NN, b0 = (r / NN) * NB;
+
+  R K[NB][D][D], rhs[D];
+  row_block<Cfg, OP>(sm, rr, P, le, a, b0, K, rhs);
+
+  const int64_t node = P.tconn[et * NN + a];
+  const int64_t id = P.ids ? (int64_t)P.ids[et] : et;
+  const int64_t moff = P.mapoff ? P.mapoff[et] : id * NN * NN;
+  const int32_t* mp = P.node_map + moff + a * NN + b0;
+  int64_t rb[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) rb[c] = P.row_ptr[D * node + c];
+#pragma unroll
+  for (int bb = 0; bb < NB; ++bb) {
+    const int64_t k = mp[bb];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int cc = 0; cc < D; ++cc) atomicAdd(P.A + rb[c] + D * k + cc, (double)K[bb][c][cc]);
+  }
+  if (b0 == 0)
+#pragma unroll
+    for (int c = 0; c < D; ++c) atomicAdd(P.b + D * node + c, (double)rhs[c]);
+}
+
+// ---------------------------------------------------------------------------
+// host dispatch
+// ---------------------------------------------------------------------------
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+static int launch_atomic(const AsmParams& P, cudaStream_t s) {
+  using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
+  const unsigned grid = grid_for(P.n, Cfg::EPC);
+  k_assemble_atomic<TYPE, SLOT, OP, PREC, SPLIT><<<grid, Cfg::THREADS, 0, s>>>(host_rule(SLOT), P);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
+template <int OP, int PREC>
+static int launch_group(int type, int tet_rule, const AsmParams& P, cudaStream_t s) {
+  // FP64 elasticity splits the columns of hex8 / prism6 over two lanes (register budget)
+  constexpr int S2 = (OP == FEA_OP_ELASTICITY && PREC == FEA_FP64) ? 2 : 1;
+  switch (type) {
+    case FEA_TET4:
+      return tet_rule ? launch_atomic<FEA_TET4, kRuleTet4, OP, PREC, 1>(P, s)
+                      : launch_atomic<FEA_TET4, kRuleTet1, OP, PREC, 1>(P, s);
+    case FEA_PYR5:
+      return launch_atomic<FEA_PYR5, kRulePyr8, OP, PREC, 1>(P, s);
+    case FEA_PRISM6:
+      return launch_atomic<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(P, s);
+    default:
+      return launch_atomic<FEA_HEX8, kRuleHex8, OP, PREC, S2>(P, s);
+  }
+}
+
+int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
+             double* b, cudaStream_t s) {
+  if (!op || !m || !row_ptr || !node_map || !A || !b) return fail(FEA_ERR_ARG, "fea_assemble: null argument");
+  if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY)
+    return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
+  if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE)
+    return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
+  if (op->scatter != FEA_SCATTER_ATOMIC)
+    return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: scatter variant not available");
+  if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
+  const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
+  if (m->pattern_ndof != D || !m->pattern_built)
+    return fail(FEA_ERR_ARG, "fea_assemble: build the pattern and map for ndof = " + std::to_string(D) + " first");
+  if (op->kind == FEA_OP_ELASTICITY) {
+    if (!(op->poisson > -1.0 && op->poisson < 0.5)) return fail(FEA_ERR_ARG, "fea_assemble: poisson must be in (-1, 0.5)");
+  }
+  const int64_t nnz = (int64_t)D * D * m->nnz_node;
+  cudaEvent_t* ev = (cudaEvent_t*)op->events;
+  const int nev = ev ? op->n_events : 0;
+  if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+  FEA_CUDA(cudaMemsetAsync(A, 0, nnz * sizeof(double), s));
+  FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
+  if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+  int launched = 0;
+
+  AsmParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.coords = m->coords;
+  P.row_ptr = row_ptr;
+  P.node_map = node_map;
+  P.A = A;
+  P.b = b;
+  P.st = m->status;
+  P.k0 = op->k0;
+  P.k2 = op->k2;
+  P.src = op->source;
+  const double E = op->young, nu = op->poisson;
+  P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  P.mu = E / (2.0 * (1.0 + nu));
+  for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
+  for (int t = 0; t < kNumTypes; ++t) {
+    const TypeGroup& g = m->group[t];
+    if (!g.n) continue;
+    P.tconn = g.conn;
+    P.ids = g.ids;
+    P.mapoff = g.mapoff;
+    P.n = g.n;
+    int rc;
+    if (op->kind == FEA_OP_DIFFUSION)
+      rc = op->precision == FEA_FP64 ? launch_group<FEA_OP_DIFFUSION, FEA_FP64>(t, op->tet_rule, P, s)
+                                     : launch_group<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE>(t, op->tet_rule, P, s);
+    else
+      rc = op->precision == FEA_FP64 ? launch_group<FEA_OP_ELASTICITY, FEA_FP64>(t, op->tet_rule, P, s)
+                                     : launch_group<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE>(t, op->tet_rule, P, s);
+    if (rc) return rc;
+    if (2 + launched < nev) FEA_CUDA(cudaEventRecord(ev[2 + launched], s));
+    ++launched;
+  }
+  return FEA_OK;
+}
+
+int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
+  if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
+  int k = 0;
+  for (int t = 0; t < kNumTypes; ++t) k += m->group[t].n > 0;
+  *n = k;
+  return FEA_OK;
+}
+
+}  // namespace fea

@@ -1,0 +1,96 @@
+// fea_internal.cuh -- definitions shared by the engine's translation units
+// (mesh handle, device status word, error helpers, launch helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fea_gb300.h"
+
+namespace fea {
+
+constexpr int kNumTypes = 4;
+constexpr int kNodesOf[kNumTypes] = {4, 5, 6, 8};
+
+__host__ __device__ constexpr int nodes_of(int t) {
+  return t == FEA_TET4 ? 4 : t == FEA_PYR5 ? 5 : t == FEA_PRISM6 ? 6 : 8;
+}
+
+// Device status word latched by kernels; read back by fea_check.
+struct DevStatus {
+  int code;                 // 0 or a negative fea_status
+  int pad;
+  unsigned long long info;  // smallest offending element / node id
+};
+
+__device__ __forceinline__ void latch_error(DevStatus* st, int code, unsigned long long id) {
+  atomicCAS(&st->code, 0, code);
+  atomicMin(&st->info, id);
+}
+
+// Per-type element group: original ids and packed connectivity.
+struct TypeGroup {
+  int64_t n = 0;            // elements of this type
+  int32_t* ids = nullptr;   // [n] original element ids (nullptr: identity, single-type mesh)
+  int32_t* conn = nullptr;  // [n * nodes_of(t)] packed connectivity, local order
+  int64_t* mapoff = nullptr;// [n] offset of the element's block in node_map (nullptr: id * nn^2)
+};
+
+}  // namespace fea
+
+struct fea_mesh {
+  int device = 0;
+  int64_t n_nodes = 0;
+  int64_t n_elems = 0;
+  int64_t conn_len = 0;
+  int64_t map_len = 0;
+  bool uniform = false;               // one element type, conn_offsets[e] = e * nn
+  int uniform_type = -1;
+  double* coords = nullptr;           // [3 n_nodes]
+  int64_t* conn_off = nullptr;        // [n_elems + 1]
+  int32_t* conn = nullptr;            // [conn_len]
+  int64_t* map_off = nullptr;         // [n_elems + 1] offsets into node_map
+  fea::TypeGroup group[fea::kNumTypes];
+  fea::DevStatus* status = nullptr;   // device status word
+  // node graph (built by fea_pattern_size)
+  int pattern_ndof = 0;               // ndof of the last fea_pattern_size (0: none)
+  bool pattern_built = false;         // fea_build_csr_pattern ran for pattern_ndof
+  int64_t nnz_node = 0;
+  int64_t* rp_node = nullptr;         // [n_nodes + 1]
+  int32_t* col_node = nullptr;        // [nnz_node]
+  int64_t* inc_off = nullptr;         // [n_nodes + 1] node -> incidences
+  int64_t* inc = nullptr;             // [conn_len] incidence = e * 16 + local index
+};
+
+namespace fea {
+
+// Thread-local error message.
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FEA_CUDA(call)                                       \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return ::fea::cuda_fail(_e, #call); \
+  } while (0)
+
+inline unsigned grid_for(int64_t n, int per_block) {
+  int64_t g = (n + per_block - 1) / per_block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// pattern.cu
+int build_node_graph(fea_mesh* m, cudaStream_t s);
+int write_csr_pattern(fea_mesh* m, int ndof, int64_t* row_ptr, int32_t* col_idx, int32_t* node_map,
+                      cudaStream_t s);
+int exclusive_scan_i32(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+
+// assemble.cu
+int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+             double* A, double* b, cudaStream_t s);
+int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n);
+
+}  // namespace fea

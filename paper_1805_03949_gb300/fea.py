@@ -1,0 +1,252 @@
+"""Thin ctypes binding of the engine's C-ABI (``include/fea_gb300.h``).
+
+The functions below carry the C names and only marshal arguments: every step
+of the assembly runs in the CUDA kernels of ``libfea_gb300.so``.  Device
+buffers are torch CUDA tensors owned by the caller; streams are torch streams
+(the current stream by default).  There is no CPU fallback: importing this
+module raises if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libfea_gb300.so")
+
+FEA_OK = 0
+FEA_ERR_ARG = -1
+FEA_ERR_OOM = -2
+FEA_ERR_CUDA = -3
+FEA_ERR_INVERTED_ELEMENT = -4
+FEA_ERR_NO_CONVERGENCE = -5
+FEA_ERR_TIMEOUT = -6
+FEA_ERR_INDEX_OVERFLOW = -7
+FEA_ERR_UNSUPPORTED = -8
+
+FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
+FEA_OP_DIFFUSION, FEA_OP_ELASTICITY = 0, 1
+FEA_FP64, FEA_FP32_INTEGRATE = 0, 1
+FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK = 0, 1, 2
+
+
+class FeaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class fea_mesh_desc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64),
+                ("coords", ctypes.c_void_p), ("types", ctypes.c_void_p),
+                ("conn_offsets", ctypes.c_void_p), ("conn", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fea_operator(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("precision", ctypes.c_int32), ("scatter", ctypes.c_int32),
+                ("tet_rule", ctypes.c_int32), ("k0", ctypes.c_double), ("k2", ctypes.c_double),
+                ("source", ctypes.c_double), ("young", ctypes.c_double), ("poisson", ctypes.c_double),
+                ("body_force", ctypes.c_double * 3), ("events", ctypes.POINTER(ctypes.c_void_p)),
+                ("n_events", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"engine library {LIB_PATH} is not built; run paper_1805_03949_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "fea_last_error": (ctypes.c_char_p, []),
+        "fea_abi_version": (I32, []),
+        "fea_mesh_upload": (I32, [ctypes.POINTER(fea_mesh_desc), P, ctypes.POINTER(P)]),
+        "fea_mesh_destroy": (I32, [P]),
+        "fea_mesh_set_coords": (I32, [P, P, I32, P]),
+        "fea_mesh_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "fea_pattern_size": (I32, [P, I32, ctypes.POINTER(I64), P]),
+        "fea_build_csr_pattern": (I32, [P, I32, P, P, P, P]),
+        "fea_assemble": (I32, [ctypes.POINTER(fea_operator), P, P, P, P, P, P]),
+        "fea_check": (I32, [P, P]),
+        "fea_assemble_launches": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
+    }
+    for name, (rt, at) in sig.items():
+        f = getattr(lib, name)
+        f.restype = rt
+        f.argtypes = at
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FEA_OK:
+        raise FeaError(rc, _lib.fea_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(None)
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fea_last_error() -> str:
+    return _lib.fea_last_error().decode()
+
+
+def fea_abi_version() -> int:
+    return int(_lib.fea_abi_version())
+
+
+def fea_mesh_upload(coords, types, conn_offsets, conn, stream=None) -> ctypes.c_void_p:
+    """Upload a mesh (numpy host arrays or contiguous CUDA tensors); returns the handle."""
+    on_device = isinstance(coords, torch.Tensor) and coords.is_cuda
+    keep = []
+    if on_device:
+        arrs = [coords.to(torch.float64).contiguous(), types.to(torch.uint8).contiguous(),
+                conn_offsets.to(torch.int64).contiguous(), conn.to(torch.int32).contiguous()]
+        ptrs = [a.data_ptr() for a in arrs]
+        keep = arrs
+    else:
+        arrs = [np.ascontiguousarray(coords, dtype=np.float64), np.ascontiguousarray(types, dtype=np.uint8),
+                np.ascontiguousarray(conn_offsets, dtype=np.int64), np.ascontiguousarray(conn, dtype=np.int32)]
+        ptrs = [a.ctypes.data for a in arrs]
+        keep = arrs
+    d = fea_mesh_desc(n_nodes=int(arrs[0].shape[0]), n_elems=int(arrs[1].shape[0]), coords=ptrs[0],
+                      types=ptrs[1], conn_offsets=ptrs[2], conn=ptrs[3], on_device=1 if on_device else 0)
+    h = ctypes.c_void_p()
+    _check(_lib.fea_mesh_upload(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    del keep
+    return h
+
+
+def fea_mesh_set_coords(h, coords, stream=None):
+    """New node coordinates: a contiguous float64 CUDA tensor, or a numpy array / CPU tensor."""
+    if isinstance(coords, torch.Tensor) and coords.is_cuda:
+        _check(_lib.fea_mesh_set_coords(h, _dptr(coords), 1, _stream(stream)))
+    else:
+        if isinstance(coords, torch.Tensor):
+            arr = coords.contiguous()
+            ptr = arr.data_ptr()
+        else:
+            arr = np.ascontiguousarray(coords, dtype=np.float64)
+            ptr = arr.ctypes.data
+        _check(_lib.fea_mesh_set_coords(h, ctypes.c_void_p(ptr), 0, _stream(stream)))
+
+
+def fea_mesh_destroy(h):
+    _check(_lib.fea_mesh_destroy(h))
+
+
+def fea_mesh_info(h):
+    n, e, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.fea_mesh_info(h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(m)))
+    return n.value, e.value, m.value
+
+
+def fea_pattern_size(h, ndof: int, stream=None) -> int:
+    nnz = ctypes.c_int64()
+    _check(_lib.fea_pattern_size(h, ndof, ctypes.byref(nnz), _stream(stream)))
+    return nnz.value
+
+
+def fea_build_csr_pattern(h, ndof: int, row_ptr, col_idx, node_map, stream=None):
+    _check(_lib.fea_build_csr_pattern(h, ndof, _dptr(row_ptr), _dptr(col_idx), _dptr(node_map), _stream(stream)))
+
+
+def fea_assemble(op: "fea_operator", h, row_ptr, node_map, A, b, stream=None):
+    _check(_lib.fea_assemble(ctypes.byref(op), h, _dptr(row_ptr), _dptr(node_map), _dptr(A), _dptr(b),
+                             _stream(stream)))
+
+
+def fea_check(h, stream=None):
+    _check(_lib.fea_check(h, _stream(stream)))
+
+
+def fea_assemble_launches(op: "fea_operator", h) -> int:
+    n = ctypes.c_int()
+    _check(_lib.fea_assemble_launches(ctypes.byref(op), h, ctypes.byref(n)))
+    return n.value
+
+
+def set_events(op: "fea_operator", events) -> None:
+    """Attach torch.cuda.Event objects (already recorded once, so they exist) as the profiling hook."""
+    if not events:
+        op.events = None
+        op.n_events = 0
+        return
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    op._event_array = arr
+    op.events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+    op.n_events = len(events)
+
+
+# ---------------------------------------------------------------------------
+# convenience: operator construction and a mesh + pattern + buffers bundle
+# ---------------------------------------------------------------------------
+
+def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER_ATOMIC, tet_rule=1,
+                  k0=1.0, k2=0.0, source=1.0, young=1.0, poisson=0.3, body_force=(1.0, 1.0, 1.0)) -> fea_operator:
+    op = fea_operator()
+    op.kind, op.precision, op.scatter, op.tet_rule = kind, precision, scatter, tet_rule
+    op.k0, op.k2, op.source = k0, k2, source
+    op.young, op.poisson = young, poisson
+    for c in range(3):
+        op.body_force[c] = body_force[c]
+    return op
+
+
+@dataclass
+class System:
+    """A mesh handle with its CSR pattern, map and value buffers on one device."""
+
+    handle: ctypes.c_void_p
+    ndof: int
+    n_nodes: int
+    n_elems: int
+    row_ptr: torch.Tensor
+    col_idx: torch.Tensor
+    node_map: torch.Tensor
+    A: torch.Tensor
+    b: torch.Tensor
+    extra: dict = field(default_factory=dict)
+
+    @classmethod
+    def from_mesh(cls, mesh, ndof: int, device="cuda", stream=None, with_cols: bool = True) -> "System":
+        h = fea_mesh_upload(mesh.coords, mesh.types, mesh.conn_offsets, mesh.conn, stream)
+        n, e, mlen = fea_mesh_info(h)
+        nnz = fea_pattern_size(h, ndof, stream)
+        rp = torch.empty(n * ndof + 1, dtype=torch.int64, device=device)
+        col = torch.empty(nnz if with_cols else 0, dtype=torch.int32, device=device)
+        nmap = torch.empty(mlen, dtype=torch.int32, device=device)
+        fea_build_csr_pattern(h, ndof, rp, col if with_cols else None, nmap, stream)
+        A = torch.empty(nnz, dtype=torch.float64, device=device)
+        b = torch.empty(n * ndof, dtype=torch.float64, device=device)
+        return cls(h, ndof, n, e, rp, col, nmap, A, b)
+
+    def assemble(self, op: fea_operator, stream=None):
+        fea_assemble(op, self.handle, self.row_ptr, self.node_map, self.A, self.b, stream)
+
+    def check(self, stream=None):
+        fea_check(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            fea_mesh_destroy(self.handle)
+            self.handle = None

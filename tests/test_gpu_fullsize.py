@@ -1,0 +1,113 @@
+"""GPU parity at the full workload sizes, in the launch configuration the benchmark times.
+
+The oracle cannot assemble 2-4.5 M elements in seconds, so the full-size
+checks are (a) closed-form properties of the whole pattern (nnz, row lengths,
+sortedness, map round trip on sampled elements) and (b) sampled rows: every
+dof row of ~30 seeded nodes (corners, edges, faces, interior) is recomputed by
+the oracle from all elements in index order and compared entry by entry.
+"""
+import numpy as np
+import pytest
+
+from paper_1805_03949_gb300 import meshgen as mg
+from tests.helpers import FP32_TOL, FP64_TOL, engine
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample_nodes(n, rng, count=24):
+    m = n + 1
+    idx = lambda i, j, k: i + m * (j + m * k)
+    fixed = [idx(0, 0, 0), idx(n, n, n), idx(n, 0, 0), idx(0, n, 5), idx(3, 0, 7), idx(n, 9, n // 2),
+             idx(n // 2, n // 2, n // 2)]
+    rnd = rng.integers(0, m ** 3, size=count).tolist()
+    return np.array(sorted(set(fixed + rnd)), dtype=np.int32)
+
+
+def _check_rows(oracle, s, mesh, nodes, op_oracle, d, tol, **params):
+    rows = oracle.assemble_rows(mesh, nodes, op_oracle, **params)
+    rp = s.row_ptr.cpu().numpy()
+    col = s.col_idx.cpu().numpy() if s.col_idx.numel() else None
+    A = s.A.cpu().numpy()
+    b = s.b.cpu().numpy()
+    worst = 0.0
+    for node, r in zip(nodes, rows):
+        for c in range(d):
+            lo, hi = rp[d * node + c], rp[d * node + c + 1]
+            if col is not None:
+                expect_cols = (d * r["cols"][:, None] + np.arange(d)[None, :]).ravel()
+                assert np.array_equal(col[lo:hi], expect_cols)
+            vals, nv = r["vals"][c], r["nvals"][c]
+            assert hi - lo == len(vals)
+            err = np.max(np.abs(A[lo:hi] - vals) / nv)
+            errb = abs(b[d * node + c] - r["b"][c]) / r["sb"][c]
+            worst = max(worst, err, errb)
+    assert worst <= tol, worst
+    return worst
+
+
+@pytest.fixture(scope="module")
+def c2():
+    fea = engine()
+    n = 128
+    mesh = mg.hex_cube(n, 0.2, 2)
+    s = fea.System.from_mesh(mesh, 3)
+    yield fea, mesh, s
+    s.close()
+
+
+def test_c2_pattern_closed_form(c2):
+    fea, mesh, s = c2
+    n = 128
+    assert s.A.numel() == 9 * (3 * n + 1) ** 3 == 513_599_625
+    rp = s.row_ptr.cpu().numpy()
+    lens = np.diff(rp)
+    assert lens.min() == 3 * 8 and lens.max() == 3 * 27           # corner node: 8 neighbours, interior: 27
+    assert np.count_nonzero(lens == 81) == 3 * (n - 1) ** 3
+    col = s.col_idx.cpu().numpy()
+    # rows sorted strictly ascending: within every row, consecutive columns increase
+    inc = np.diff(col)
+    starts = rp[1:-1]
+    inc[starts - 1] = 1                                           # row boundaries are not compared
+    assert np.all(inc > 0)
+    # map round trip on sampled elements
+    rng = np.random.default_rng(0)
+    nmap = s.node_map.cpu().numpy().reshape(-1, 8, 8)
+    conn = mesh.conn.reshape(-1, 8)
+    for e in rng.integers(0, mesh.n_elems, size=200):
+        for a in range(8):
+            i = conn[e, a]
+            for bb in range(8):
+                assert col[rp[3 * i] + 3 * nmap[e, a, bb]] == 3 * conn[e, bb]
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_c2_sampled_rows(oracle, c2, precision):
+    fea, mesh, s = c2
+    op = fea.make_operator(kind=1, precision=precision, scatter=0, young=1.0, poisson=0.3)
+    s.assemble(op)
+    s.check()
+    nodes = _sample_nodes(128, np.random.default_rng(11))
+    _check_rows(oracle, s, mesh, nodes, oracle.OP_ELASTICITY, 3, FP64_TOL if precision == 0 else FP32_TOL,
+                young=1.0, poisson=0.3)
+    # global invariants that hold at any size: sum of b per component = volume = 1
+    bsum = s.b.view(-1, 3).sum(dim=0).cpu().numpy()
+    assert np.allclose(bsum, 1.0, rtol=0, atol=1e-9 if precision == 0 else 1e-5)
+
+
+def test_c3_hybrid_sampled_rows(oracle):
+    fea = engine()
+    mesh = mg.hybrid_cube(100, 3)
+    s = fea.System.from_mesh(mesh, 1, with_cols=True)
+    try:
+        rng = np.random.default_rng(3)
+        nodes = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, size=24), [0, mesh.n_nodes - 1]]))
+        nodes = nodes.astype(np.int32)
+        for precision, tol in ((1, FP32_TOL), (0, FP64_TOL)):
+            s.assemble(fea.make_operator(kind=0, precision=precision, tet_rule=1, k0=1.0, k2=1.0, source=1.0))
+            s.check()
+            _check_rows(oracle, s, mesh, nodes, oracle.OP_DIFFUSION, 1, tol, tet_rule=1, k0=1.0, k2=1.0,
+                        source=1.0)
+            assert abs(float(s.b.sum()) - 1.0) < (1e-9 if precision == 0 else 1e-6)
+    finally:
+        s.close()

@@ -415,6 +415,9 @@ def test_hybrid_mesh_invariants(oracle):
     assert np.all(np.abs(rs) <= 1e-14 * Srow)
     assert _symmetric(r) == 0.0
     assert np.all(r["SA"] >= np.abs(r["A"]))
+    assert np.all(r["NA"] >= r["SA"] * (1 - 1e-14))          # Cauchy-Schwarz: normwise >= componentwise
+    re = oracle.assemble(mesh, oracle.OP_ELASTICITY, young=1.0, poisson=0.3)
+    assert np.all(re["NA"] >= re["SA"] * (1 - 1e-14))
 
 
 def test_rows_function_equals_full_assembly(oracle):
