@@ -188,6 +188,29 @@ int fea_build_csr_pattern(fea_mesh* mesh, int ndof, int64_t* row_ptr_d, int32_t*
 int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d,
                  const int32_t* node_map_d, double* A_vals_d, double* b_d, void* stream);
 
+/* CSR row pointers from row lengths, allocating nothing on the device.
+ * The paper has no counterpart: this is a service for callers that cannot let
+ * a library allocate device memory -- applications that reserve all of the
+ * GPU's memory for their own pool at start-up, or that run this step where an
+ * allocation would have to go through their allocator or would synchronize
+ * the device.  The same scan inside fea_pattern_size takes its scratch from a
+ * stream-ordered allocation; this entry point instead uses a fixed 128 KB
+ * array compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *  counts_d   int32 [n] row lengths (device)
+ *  row_ptr_d  int64 [n + 1] output (device): row_ptr_d[0] = 0,
+ *             row_ptr_d[i + 1] = counts_d[0] + ... + counts_d[i]
+ *  n          0 <= n <= 67,108,864 (16,384 tiles of 4,096 rows); larger n is
+ *             rejected with FEA_ERR_UNSUPPORTED before any work is queued
+ * Stream-ordered.  The first call on a device looks up the scratch array's
+ * device address (once per device, with that device current); make that
+ * first call before any stream capture.  Every call shares the one scratch
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads on one device) race: order them.  The scratch needs
+ * no clearing between calls (every slot read is written first in the same
+ * call). */
+int fea_row_ptr_from_counts_noalloc(const int32_t* counts_d, int64_t n, int64_t* row_ptr_d, void* stream);
+
 /* Number of kernels one fea_assemble call with this operator launches on this
  * mesh (after its pattern is built).  Host call. */
 int fea_assemble_launches(const fea_operator* op, const fea_mesh* mesh, int* n_kernels);

@@ -14,6 +14,8 @@
 // Everything is integer work and deterministic: the atomics of step 1 only
 // decide the order of the incidence lists, which no output depends on.
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "fea_internal.cuh"
 
@@ -366,4 +368,65 @@ int write_csr_pattern(fea_mesh* m, int ndof, int64_t* row_ptr, int32_t* col_idx,
   return FEA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Row pointers from row lengths without any device allocation.
+//
+// The scan above takes its per-tile partial sums from a stream-ordered
+// allocation.  Callers that hand all device memory to their own pool up
+// front, or that must not let a library allocate on their behalf, use
+// fea_row_ptr_from_counts_noalloc instead: the tile sums live in the
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxTiles = 16384;                      // 128 KB of tile sums
+constexpr int64_t kNoAllocMaxCounts = kNoAllocMaxTiles * kScanTile;  // 67,108,864 rows
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) int64_t g_noalloc_tiles[kNoAllocMaxTiles];
+
+static std::mutex g_noalloc_mutex;
+static int64_t* g_noalloc_ptr[kNoAllocMaxDevices];  // device address of g_noalloc_tiles, per device
+
+// Device address of the scratch array on the current device: taken once per
+// device, with that device current, on the first call there.
+static int noalloc_scratch(int64_t** out) {
+  int dev = 0;
+  FEA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(FEA_ERR_UNSUPPORTED, "fea_row_ptr_from_counts_noalloc: device index " + std::to_string(dev) +
+                                         " beyond the supported " + std::to_string(kNoAllocMaxDevices));
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_tiles)");
+    g_noalloc_ptr[dev] = (int64_t*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FEA_OK;
+}
+
 }  // namespace fea
+
+extern "C" int fea_row_ptr_from_counts_noalloc(const int32_t* counts, int64_t n, int64_t* row_ptr, void* stream) {
+  using namespace fea;
+  if (n < 0 || !row_ptr || (n > 0 && !counts))
+    return fail(FEA_ERR_ARG, "fea_row_ptr_from_counts_noalloc: null pointer or negative length");
+  if (n > kNoAllocMaxCounts)
+    return fail(FEA_ERR_UNSUPPORTED, "fea_row_ptr_from_counts_noalloc: " + std::to_string(n) +
+                                         " rows exceed the fixed scratch limit of " +
+                                         std::to_string(kNoAllocMaxCounts));
+  int64_t* tiles = nullptr;
+  int rc = noalloc_scratch(&tiles);
+  if (rc != FEA_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  if (ntiles < 1) ntiles = 1;
+  // every tile sum read below is written first by k_scan_reduce, so the
+  // scratch left by an earlier call needs no clearing
+  k_scan_reduce<<<(unsigned)ntiles, kScanBlock, 0, s>>>(counts, n, tiles);
+  k_scan_tiles<<<1, kScanBlock, 0, s>>>(tiles, ntiles);
+  k_scan_apply<<<(unsigned)ntiles, kScanBlock, 0, s>>>(counts, n, tiles, row_ptr);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}

@@ -72,6 +72,7 @@ def _load():
         "fea_assemble": (I32, [ctypes.POINTER(fea_operator), P, P, P, P, P, P]),
         "fea_check": (I32, [P, P]),
         "fea_assemble_launches": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
+        "fea_row_ptr_from_counts_noalloc": (I32, [P, I64, P, P]),
     }
     for name, (rt, at) in sig.items():
         f = getattr(lib, name)
@@ -177,6 +178,16 @@ def fea_assemble(op: "fea_operator", h, row_ptr, node_map, A, b, stream=None):
 
 def fea_check(h, stream=None):
     _check(_lib.fea_check(h, _stream(stream)))
+
+
+def fea_row_ptr_from_counts_noalloc(counts, row_ptr, stream=None):
+    """Row pointers from int32 row lengths into ``row_ptr`` (n + 1 int64), no device allocation.
+
+    For callers that cannot let the library allocate device memory; see the
+    declaration in fea_gb300.h for the size limit and the shared scratch.
+    """
+    _check(_lib.fea_row_ptr_from_counts_noalloc(_dptr(counts), int(counts.numel()), _dptr(row_ptr),
+                                                _stream(stream)))
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:
