@@ -78,8 +78,14 @@ typedef enum {
 typedef enum {
   FEA_SCATTER_ATOMIC = 0, /* FP64 atomic adds into A and b (the paper's Alg. "no coloring") */
   FEA_SCATTER_COLOR = 1,  /* element coloring, plain read-modify-write per color (Alg. "coloring") */
-  FEA_SCATTER_BLOCK = 2   /* locality blocks accumulated in shared memory, block-boundary
+  FEA_SCATTER_BLOCK = 2,  /* locality blocks accumulated in shared memory, block-boundary
                              entries resolved globally (Alg. "local partitioning" / "multideps") */
+  FEA_SCATTER_ROWS = 3    /* owner-computes full rows (Sec. 3.1 full-row decomposition with halo
+                             elements, applied per CTA): each CTA owns a block of nodes along a
+                             Morton curve, recomputes the geometry of the elements touching them and
+                             writes every entry of its rows once with plain stores -- no atomics, no
+                             zero fill, bitwise reproducible.  The first call per (mesh, ndof) builds
+                             the block plan on the host (synchronous); later calls are stream-ordered. */
 } fea_scatter;
 
 /* Mesh description for fea_mesh_upload.  coords is xyz per node (AoS,
@@ -210,6 +216,17 @@ int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_
  * no clearing between calls (every slot read is written first in the same
  * call). */
 int fea_row_ptr_from_counts_noalloc(const int32_t* counts_d, int64_t n, int64_t* row_ptr_d, void* stream);
+
+/* Nodes per CTA block of FEA_SCATTER_ROWS (default 64; 1..512).  A change
+ * drops the current plan; the next ROWS assembly rebuilds it.  Host call. */
+int fea_mesh_set_rows_block(fea_mesh* mesh, int block_nodes);
+
+/* Statistics of the current FEA_SCATTER_ROWS plan (zeros if none):
+ * info[0] blocks, [1] nodes per block, [2] max local nodes of a block,
+ * [3] max halo elements of a block, [4] entry tasks, [5] element
+ * contributions, [6] halo elements (with repeats), [7] plan bytes on the
+ * device.  Host call. */
+int fea_rows_plan_info(const fea_mesh* mesh, int64_t info[8]);
 
 /* Number of kernels one fea_assemble call with this operator launches on this
  * mesh (after its pattern is built).  Host call. */

@@ -197,30 +197,6 @@ struct TileSmem {
   int flag[EPC];            // FP32 mode: element is distorted -> FP64 geometry
 };
 
-__device__ __forceinline__ void cofactors(const double J[3][3], double C[3][3]) {
-  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-}
-
-__device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {
-  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-}
-
 // FP64 geometry of point q of element le; results rounded to the tile type R.
 template <int OP, int NN, typename Smem>
 __device__ __forceinline__ void geometry_fp64(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
@@ -426,6 +402,11 @@ __device__ __forceinline__ void row_block(const typename Cfg::Smem& sm, const Re
   }
 }
 
+// FP64 value of a contribution: exact integer widening of FP32 (keeps the
+// FP64 pipe free), identity for FP64
+__device__ __forceinline__ double widen(float x) { return f32_to_f64_exact(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // ATOMIC scatter: FP64 atomic adds of each row block (Alg. "no coloring")
 template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
 __global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__ RefRule rr,
@@ -462,11 +443,11 @@ __global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int cc = 0; cc < D; ++cc) atomicAdd(P.A + rb[c] + D * k + cc, (double)K[bb][c][cc]);
+      for (int cc = 0; cc < D; ++cc) atomicAdd(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
   }
   if (b0 == 0)
 #pragma unroll
-    for (int c = 0; c < D; ++c) atomicAdd(P.b + D * node + c, (double)rhs[c]);
+    for (int c = 0; c < D; ++c) atomicAdd(P.b + D * node + c, widen(rhs[c]));
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +486,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
   if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
-  if (op->scatter != FEA_SCATTER_ATOMIC)
+  if (op->scatter != FEA_SCATTER_ATOMIC && op->scatter != FEA_SCATTER_ROWS)
     return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: scatter variant not available");
   if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
   const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
@@ -517,6 +498,21 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   const int64_t nnz = (int64_t)D * D * m->nnz_node;
   cudaEvent_t* ev = (cudaEvent_t*)op->events;
   const int nev = ev ? op->n_events : 0;
+  if (op->scatter == FEA_SCATTER_ROWS) {
+    // every entry of A is written exactly once by its owner; only b rows of
+    // nodes without elements would stay unwritten, so b alone is cleared
+    RowsPlan* plan = nullptr;
+    int prc = ensure_rows_plan(m, D, op->precision, s, &plan);  // host work on the first call only
+    if (prc) return prc;
+    if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+    FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
+    if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+    int launched = 0;
+    int rc = assemble_rows(op, m, row_ptr, A, b, s, &launched);
+    if (rc) return rc;
+    if (nev > 2) FEA_CUDA(cudaEventRecord(ev[2], s));
+    return FEA_OK;
+  }
   if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
   FEA_CUDA(cudaMemsetAsync(A, 0, nnz * sizeof(double), s));
   FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
@@ -561,6 +557,10 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
 
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
   if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
+  if (op->scatter == FEA_SCATTER_ROWS) {
+    *n = 1;
+    return FEA_OK;
+  }
   int k = 0;
   for (int t = 0; t < kNumTypes; ++t) k += m->group[t].n > 0;
   *n = k;

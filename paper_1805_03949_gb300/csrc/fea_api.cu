@@ -52,6 +52,7 @@ static void free_mesh(fea_mesh* m) {
   cudaFree(m->col_node);
   cudaFree(m->inc_off);
   cudaFree(m->inc);
+  drop_rows_plans(m);
   delete m;
 }
 
@@ -245,6 +246,34 @@ int fea_build_csr_pattern(fea_mesh* m, int ndof, int64_t* row_ptr, int32_t* col_
 int fea_assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
                  double* A, double* b, void* stream) {
   return fea::assemble(op, m, row_ptr, node_map, A, b, (cudaStream_t)stream);
+}
+
+int fea_mesh_set_rows_block(fea_mesh* m, int block_nodes) {
+  if (!m) return fail(FEA_ERR_ARG, "fea_mesh_set_rows_block: null handle");
+  if (block_nodes < 1 || block_nodes > 512) return fail(FEA_ERR_ARG, "fea_mesh_set_rows_block: block size in [1, 512]");
+  if (block_nodes != m->rows_block_nodes) {
+    cudaDeviceSynchronize();
+    drop_rows_plans(m);
+  }
+  m->rows_block_nodes = block_nodes;
+  return FEA_OK;
+}
+
+int fea_rows_plan_info(const fea_mesh* m, int64_t info[8]) {
+  if (!m || !info) return fail(FEA_ERR_ARG, "fea_rows_plan_info: null argument");
+  for (int k = 0; k < 8; ++k) info[k] = 0;
+  const fea::RowsPlan* pp = m->rows[1] ? m->rows[1] : m->rows[0];
+  if (!pp) return FEA_OK;
+  const fea::RowsPlan& P = *pp;
+  info[0] = P.n_blocks;
+  info[1] = P.block_nodes;
+  info[2] = P.max_local;
+  info[3] = P.max_helem;
+  info[4] = P.n_tasks;
+  info[5] = P.n_contrib;
+  info[6] = P.n_helem_total;
+  info[7] = (int64_t)P.bytes;
+  return FEA_OK;
 }
 
 int fea_assemble_launches(const fea_operator* op, const fea_mesh* m, int* n_kernels) {

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "fea_gb300.h"
+#include "rows.cuh"
 
 namespace fea {
 
@@ -62,6 +63,9 @@ struct fea_mesh {
   int32_t* col_node = nullptr;        // [nnz_node]
   int64_t* inc_off = nullptr;         // [n_nodes + 1] node -> incidences
   int64_t* inc = nullptr;             // [conn_len] incidence = e * 16 + local index
+  // owner-computes row assembly (FEA_SCATTER_ROWS)
+  fea::RowsPlan* rows[2] = {nullptr, nullptr};  // per precision (FEA_FP64, FEA_FP32_INTEGRATE)
+  int rows_block_nodes = 64;
 };
 
 namespace fea {

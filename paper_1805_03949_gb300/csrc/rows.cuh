@@ -1,0 +1,68 @@
+// rows.cuh -- plan of the owner-computes row assembly (see rows.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "fea_gb300.h"
+
+namespace fea {
+
+constexpr int kRowsMaxHalo = 1024;            // halo elements per block (10-bit index in a contributor)
+constexpr int kRowsMaxOwned = 255;            // owned nodes per block (8-bit index in a task)
+constexpr size_t kRowsMaxSmem = 227 * 1024;   // dynamic shared memory of one CTA
+constexpr int kRowsGStride = 193;             // values per halo element in the gradient array (8 x 8 x 3 + 1:
+                                              // the odd stride spreads consecutive elements over the banks)
+constexpr int kRowsQStride = 9;               // values per halo element in the per-point arrays
+constexpr int kRowsDStride = 23;              // FP32 relative coordinates per halo element (7 x 3 + x_0 + pad)
+constexpr uint8_t kTaskDiag = 1;              // entry (i, i): also accumulates b_i
+constexpr uint8_t kTaskTranspose = 2;         // j is owned too: write the transposed block to row j
+
+// One entry block (i, j) of an owned row i: node j sits at slot k of row i
+// (and i at slot kt of row j when the transpose is written).  Its element
+// contributions are nc codes (halo element << 6 | a << 3 | b) at coff.
+struct RowTask {
+  uint8_t li, nc, flags, pad;
+  uint16_t k, kt, lj, coff;
+};
+static_assert(sizeof(RowTask) == 12, "RowTask layout");
+
+struct RowBlock {
+  int64_t lnode_off, helem_off, task_off, contrib_off;
+  uint16_t n_owned, n_local, n_helem, pad;
+  int32_t n_tasks;
+  uint32_t task_bytes, contrib_bytes;  // padded sizes of the two lists (multiples of 16)
+};
+
+struct RowsPlan {
+  int ndof = 0;
+  int block_nodes = 0;      // cap on owned nodes per block
+  int halo_cap = 0;         // cap on halo elements per block (a single node may exceed it)
+  bool all_hex = false;     // every element is a hex8: the kernel specialised for it applies
+  int64_t n_blocks = 0;
+  int max_local = 0, max_helem = 0, max_owned = 0;
+  int64_t max_tasks = 0, max_contrib = 0;   // padded list lengths of the largest block
+  int64_t n_tasks = 0, n_contrib = 0, n_helem_total = 0;
+  size_t bytes = 0;
+  RowBlock* blocks = nullptr;
+  int32_t* lnodes = nullptr;      // per block: owned nodes, then the other nodes of its halo elements
+  int32_t* helem_id = nullptr;    // original element id of every halo element
+  uint8_t* helem_type = nullptr;
+  uint16_t* helem_ln = nullptr;   // [halo element][8] local node ids
+  RowTask* tasks = nullptr;
+  uint16_t* contrib = nullptr;
+};
+
+int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaStream_t s, RowsPlan** out);
+// the plan for (ndof, precision), built on first use with a halo cap that lets
+// two CTAs share an SM; if a block still does not fit, the node cap is halved
+int ensure_rows_plan(fea_mesh* m, int ndof, int precision, cudaStream_t s, RowsPlan** out);
+void drop_rows_plans(fea_mesh* m);
+void free_rows_plan(RowsPlan* P);
+size_t rows_smem_bytes(int precision, int max_local, int max_helem);
+int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
+                  cudaStream_t s, int* launched);
+
+}  // namespace fea

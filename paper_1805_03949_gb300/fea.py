@@ -31,7 +31,7 @@ FEA_ERR_UNSUPPORTED = -8
 FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
 FEA_OP_DIFFUSION, FEA_OP_ELASTICITY = 0, 1
 FEA_FP64, FEA_FP32_INTEGRATE = 0, 1
-FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK = 0, 1, 2
+FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS = 0, 1, 2, 3
 
 
 class FeaError(RuntimeError):
@@ -73,6 +73,8 @@ def _load():
         "fea_check": (I32, [P, P]),
         "fea_assemble_launches": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_row_ptr_from_counts_noalloc": (I32, [P, I64, P, P]),
+        "fea_mesh_set_rows_block": (I32, [P, I32]),
+        "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
     }
     for name, (rt, at) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +190,17 @@ def fea_row_ptr_from_counts_noalloc(counts, row_ptr, stream=None):
     """
     _check(_lib.fea_row_ptr_from_counts_noalloc(_dptr(counts), int(counts.numel()), _dptr(row_ptr),
                                                 _stream(stream)))
+
+
+def fea_mesh_set_rows_block(h, block_nodes: int):
+    _check(_lib.fea_mesh_set_rows_block(h, int(block_nodes)))
+
+
+def fea_rows_plan_info(h) -> dict:
+    arr = (ctypes.c_int64 * 8)()
+    _check(_lib.fea_rows_plan_info(h, arr))
+    keys = ["blocks", "block_nodes", "max_local", "max_halo", "tasks", "contributions", "halo_elements", "bytes"]
+    return dict(zip(keys, list(arr)))
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:

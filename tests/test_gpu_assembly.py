@@ -60,13 +60,19 @@ CASES = {
 }
 
 
-def _run_case(fea, oracle, name, precision):
+SCATTERS = {"atomic": 0, "rows": 3}
+
+
+def _run_case(fea, oracle, name, precision, scatter=0, block_nodes=None):
     factory, kind, oop, tet_rule, params = CASES[name]
     mesh = factory()
     ndof = 1 if kind == 0 else 3
     s = fea.System.from_mesh(mesh, ndof)
     try:
-        op = fea.make_operator(kind=kind, precision=precision, tet_rule=tet_rule, **params)
+        if block_nodes:
+            fea.fea_mesh_set_rows_block(s.handle, block_nodes)
+        op = fea.make_operator(kind=kind, precision=precision, scatter=scatter, tet_rule=tet_rule, **params)
+        s.A.fill_(float("nan"))                     # every entry must be written
         s.assemble(op)
         s.check()
         ref = oracle.assemble(mesh, oop, tet_rule=tet_rule, **params)
@@ -75,11 +81,12 @@ def _run_case(fea, oracle, name, precision):
         s.close()
 
 
+@pytest.mark.parametrize("scatter", list(SCATTERS))
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", [0, 1])
-def test_assembly_matches_oracle(oracle, name, precision):
+def test_assembly_matches_oracle(oracle, name, precision, scatter):
     fea = engine()
-    A, b, ref = _run_case(fea, oracle, name, precision)
+    A, b, ref = _run_case(fea, oracle, name, precision, SCATTERS[scatter])
     tol = FP64_TOL if precision == 0 else FP32_TOL
     errA, zA = err_vs_oracle(A, ref["A"], ref["NA"])
     errb, zb = err_vs_oracle(b, ref["b"], ref["Nb"])
@@ -121,5 +128,45 @@ def test_invalid_arguments_rejected_on_host():
             s.assemble(fea.make_operator(kind=1))
         with pytest.raises(fea.FeaError):
             s.assemble(fea.make_operator(kind=0, tet_rule=7))
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("block_nodes", [1, 7, 64, 255])
+@pytest.mark.parametrize("name", ["hybrid6_diffusion", "hybrid5_elasticity", "stretched_hex_elasticity"])
+def test_rows_block_sizes(oracle, name, block_nodes):
+    """Owner blocks of any size (one node, ragged, the default, many) give the same system."""
+    fea = engine()
+    A, b, ref = _run_case(fea, oracle, name, 1, scatter=3, block_nodes=block_nodes)
+    errA, _ = err_vs_oracle(A, ref["A"], ref["NA"])
+    errb, _ = err_vs_oracle(b, ref["b"], ref["Nb"])
+    assert errA <= FP32_TOL and errb <= FP32_TOL, (errA, errb)
+
+
+def test_rows_is_deterministic_and_symmetric():
+    """ROWS writes every entry once with plain stores: bitwise reproducible.
+
+    Entries whose two nodes share an owner block are computed once and written
+    to both triangles (bitwise symmetric); entries between blocks are computed
+    by each owner in its own order, so the matrix is symmetric to rounding.
+    """
+    fea = engine()
+    import torch
+    mesh = mg.hex_cube(9, 0.2, 4)
+    s = fea.System.from_mesh(mesh, 3)
+    try:
+        op = fea.make_operator(kind=1, precision=1, scatter=3)
+        s.assemble(op)
+        A1 = s.A.clone()
+        s.assemble(op)
+        assert torch.equal(A1, s.A)
+        import scipy.sparse as sps
+        M = sps.csr_matrix((s.A.cpu().numpy(), s.col_idx.cpu().numpy(), s.row_ptr.cpu().numpy()))
+        asym = abs(M - M.T).max()
+        assert asym <= 1e-6 * abs(M).max()
+        exact = (M - M.T).count_nonzero()
+        assert exact < M.nnz // 2                     # most entries are computed once for both triangles
+        info = fea.fea_rows_plan_info(s.handle)
+        assert info["blocks"] >= -(-mesh.n_nodes // 64) and info["tasks"] > 0
     finally:
         s.close()

@@ -43,6 +43,7 @@ def _check_rows(oracle, s, mesh, nodes, op_oracle, d, tol, **params):
             errb = abs(b[d * node + c] - r["b"][c]) / r["sb"][c]
             worst = max(worst, err, errb)
     assert worst <= tol, worst
+    assert not np.isnan(A).any()                                  # every entry was written
     return worst
 
 
@@ -81,10 +82,12 @@ def test_c2_pattern_closed_form(c2):
                 assert col[rp[3 * i] + 3 * nmap[e, a, bb]] == 3 * conn[e, bb]
 
 
+@pytest.mark.parametrize("scatter", [3, 0])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_c2_sampled_rows(oracle, c2, precision):
+def test_c2_sampled_rows(oracle, c2, precision, scatter):
     fea, mesh, s = c2
-    op = fea.make_operator(kind=1, precision=precision, scatter=0, young=1.0, poisson=0.3)
+    op = fea.make_operator(kind=1, precision=precision, scatter=scatter, young=1.0, poisson=0.3)
+    s.A.fill_(float("nan"))
     s.assemble(op)
     s.check()
     nodes = _sample_nodes(128, np.random.default_rng(11))
@@ -103,8 +106,10 @@ def test_c3_hybrid_sampled_rows(oracle):
         rng = np.random.default_rng(3)
         nodes = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, size=24), [0, mesh.n_nodes - 1]]))
         nodes = nodes.astype(np.int32)
-        for precision, tol in ((1, FP32_TOL), (0, FP64_TOL)):
-            s.assemble(fea.make_operator(kind=0, precision=precision, tet_rule=1, k0=1.0, k2=1.0, source=1.0))
+        for precision, tol, scatter in ((1, FP32_TOL, 3), (0, FP64_TOL, 3), (1, FP32_TOL, 0)):
+            s.A.fill_(float("nan"))
+            s.assemble(fea.make_operator(kind=0, precision=precision, scatter=scatter, tet_rule=1, k0=1.0, k2=1.0,
+                                         source=1.0))
             s.check()
             _check_rows(oracle, s, mesh, nodes, oracle.OP_DIFFUSION, 1, tol, tet_rule=1, k0=1.0, k2=1.0,
                         source=1.0)
