@@ -510,7 +510,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     int launched = 0;
     int rc = assemble_rows(op, m, row_ptr, A, b, s, &launched);
     if (rc) return rc;
-    if (nev > 2) FEA_CUDA(cudaEventRecord(ev[2], s));
+    for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));  // all kernels are done here
     return FEA_OK;
   }
   if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
@@ -558,7 +558,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
   if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
   if (op->scatter == FEA_SCATTER_ROWS) {
-    *n = 1;
+    *n = geometry_launches(m) + 1;  // geometry pass per element type, then the row kernel
     return FEA_OK;
   }
   int k = 0;

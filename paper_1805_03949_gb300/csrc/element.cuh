@@ -77,6 +77,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 // The FP64 value of hi + lo (one final rounding), with integer instructions.
 __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+  if (lo == 0.0f) return f32_to_f64_exact(hi);  // a single term: exact widening
   {  // renormalise so that |lo| <= ulp(hi) / 2
     const float s = hi + lo;
     const float bb = s - hi;

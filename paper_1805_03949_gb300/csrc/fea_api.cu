@@ -53,6 +53,8 @@ static void free_mesh(fea_mesh* m) {
   cudaFree(m->inc_off);
   cudaFree(m->inc);
   drop_rows_plans(m);
+  cudaFree(m->geo[0]);
+  cudaFree(m->geo[1]);
   delete m;
 }
 

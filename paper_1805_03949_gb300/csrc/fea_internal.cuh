@@ -8,6 +8,7 @@
 #include <string>
 
 #include "fea_gb300.h"
+#include "geometry.cuh"
 #include "rows.cuh"
 
 namespace fea {
@@ -65,6 +66,7 @@ struct fea_mesh {
   int64_t* inc = nullptr;             // [conn_len] incidence = e * 16 + local index
   // owner-computes row assembly (FEA_SCATTER_ROWS)
   fea::RowsPlan* rows[2] = {nullptr, nullptr};  // per precision (FEA_FP64, FEA_FP32_INTEGRATE)
+  void* geo[2] = {nullptr, nullptr};            // geometry records per precision (geometry.cu)
   int rows_block_nodes = 64;
 };
 

@@ -33,8 +33,16 @@ struct RowBlock {
   int64_t lnode_off, helem_off, task_off, contrib_off;
   uint16_t n_owned, n_local, n_helem, pad;
   int32_t n_tasks;
-  uint32_t task_bytes, contrib_bytes;  // padded sizes of the two lists (multiples of 16)
+  uint32_t task_bytes, contrib_bytes, helem_bytes;  // padded list sizes (multiples of 16)
 };
+
+// byte offsets of one block's working set in dynamic shared memory
+struct RowsLayout {
+  uint32_t recs, rs, tasks, contrib, hid, bar, total;
+};
+
+constexpr int kRowsRecSmem = 212;     // floats per staged record (208 + 4: 16-byte multiple, spreads banks)
+constexpr int kRowsStageHalo = 108;   // halo cap when records are staged (two CTAs per SM)
 
 struct RowsPlan {
   int ndof = 0;
@@ -43,7 +51,7 @@ struct RowsPlan {
   bool all_hex = false;     // every element is a hex8: the kernel specialised for it applies
   int64_t n_blocks = 0;
   int max_local = 0, max_helem = 0, max_owned = 0;
-  int64_t max_tasks = 0, max_contrib = 0;   // padded list lengths of the largest block
+  int64_t max_tasks = 0, max_contrib = 0, max_helem_padded = 0;  // padded list lengths of the largest block
   int64_t n_tasks = 0, n_contrib = 0, n_helem_total = 0;
   size_t bytes = 0;
   RowBlock* blocks = nullptr;
@@ -61,7 +69,7 @@ int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaSt
 int ensure_rows_plan(fea_mesh* m, int ndof, int precision, cudaStream_t s, RowsPlan** out);
 void drop_rows_plans(fea_mesh* m);
 void free_rows_plan(RowsPlan* P);
-size_t rows_smem_bytes(int precision, int max_local, int max_helem);
+RowsLayout rows_layout(const RowsPlan& P, bool stage);
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
                   cudaStream_t s, int* launched);
 

@@ -1,0 +1,345 @@
+// rows_kernel.cu -- the CTA kernel of the owner-computes row assembly.
+//
+// One CTA owns one node block of the plan built in rows.cu.  Its task list
+// (one task per entry block (i, j) of its rows), the element-contribution
+// codes and the ids of its halo elements arrive by TMA bulk copy into shared
+// memory; the per-element data -- scaled gradients g^_a(q), weights and k(x_q)
+// -- come from the geometry records written by the geometry pass (read through
+// L1, so the records of halo elements shared by neighbouring blocks are
+// fetched from L2 once per block rather than recomputed).
+//
+// Task (i, j): for each contributing element e (node i at local a, j at b)
+//   M_e = sum_q g^_a(q) (x) g^_b(q),   K_e = lam M_e + mu M_e^T + mu tr(M_e) I
+// (diffusion: K_e = sum_q k(x_q) g^_a . g^_b); the K_e are summed as an FP32
+// TwoSum pair (FP32_INTEGRATE) or in FP64, rounded once to FP64 and written to
+// row i -- and, transposed, to row j when j belongs to the same block.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+
+#include "element.cuh"
+#include "fea_internal.cuh"
+#include "geometry.cuh"
+#include "rows.cuh"
+
+namespace fea {
+
+struct RowsArgs {
+  const RowBlock* blocks;
+  const int32_t* lnodes;
+  const uint8_t* helem_type;
+  const RowTask* tasks;
+  const uint16_t* contrib;
+  const int32_t* helem_id;
+  const int64_t* row_ptr;
+  const void* rec;          // geometry records (float or double, kRecStride values per element)
+  double* A;
+  double* b;
+  DevStatus* st;
+  int64_t n_blocks;
+  int tet_nq;               // quadrature points of tet4 (1 or 4)
+  RowsLayout L;
+  double lam, mu, src, f[3];
+  float Ntab[kNumRules][8][8];    // N_a(q) per rule slot, for the right-hand side
+  double Ntab64[kNumRules][8][8];
+};
+
+// --- TMA bulk copy global -> shared with an mbarrier (bounded wait) --------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; gives up after a bounded number of
+// polls (each try_wait suspends for a bounded time) and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ int rule_slot_of(int type, int tet_nq) {
+  return type == FEA_TET4 ? (tet_nq == 1 ? kRuleTet1 : kRuleTet4)
+                          : type == FEA_PYR5 ? kRulePyr8 : type == FEA_PRISM6 ? kRulePrism6 : kRuleHex8;
+}
+
+// accumulator of one entry: FP64 sums, or FP32 pairs (hi, lo)
+template <int PREC>
+struct Acc;
+template <>
+struct Acc<FEA_FP64> {
+  double v = 0.0;
+  __device__ __forceinline__ void set(double x) { v = x; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct Acc<FEA_FP32_INTEGRATE> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void set(float x) { hi = x; lo = 0.0f; }
+  __device__ __forceinline__ void add(float x) { two_sum_acc(hi, lo, x); }
+  __device__ __forceinline__ double value() const { return ff_to_f64(hi, lo); }
+};
+
+// element data: staged in shared memory, or read through L1
+template <bool STAGE, typename R>
+__device__ __forceinline__ R ld_rec(const R* p) {
+  if constexpr (STAGE)
+    return *p;
+  else
+    return __ldg(p);
+}
+
+// HEX: every element is a hex8 with 8 points (compile-time loop bounds).
+// STAGE: the halo elements' records are bulk-copied into shared memory (FP32).
+template <int OP, int PREC, bool HEX, bool STAGE>
+__global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant__ RowsArgs P) {
+  using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
+  constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
+  static_assert(!STAGE || PREC != FEA_FP64, "records are staged in FP32 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* s_recs = reinterpret_cast<R*>(smem_raw + P.L.recs);
+  int64_t* s_rs = reinterpret_cast<int64_t*>(smem_raw + P.L.rs);
+  RowTask* s_tasks = reinterpret_cast<RowTask*>(smem_raw + P.L.tasks);
+  uint16_t* s_contrib = reinterpret_cast<uint16_t*>(smem_raw + P.L.contrib);
+  int32_t* s_hid = reinterpret_cast<int32_t*>(smem_raw + P.L.hid);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem_raw + P.L.bar);
+  const R* rec = reinterpret_cast<const R*>(P.rec);
+  if (threadIdx.x == 0) mbar_init(s_bar);
+  __syncthreads();
+  uint32_t parity = 0;
+  for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, parity ^= 1u) {
+    const RowBlock H = P.blocks[blk];
+    if (threadIdx.x < 32) {
+      const uint32_t rec_bytes = STAGE ? (uint32_t)(4 * kRecStride) * H.n_helem : 0u;
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order earlier reads of the buffers
+        mbar_expect_tx(s_bar, H.task_bytes + H.contrib_bytes + H.helem_bytes + rec_bytes);
+        if (H.task_bytes) bulk_copy_g2s(s_tasks, P.tasks + H.task_off, H.task_bytes, s_bar);
+        if (H.contrib_bytes) bulk_copy_g2s(s_contrib, P.contrib + H.contrib_off, H.contrib_bytes, s_bar);
+        if (H.helem_bytes) bulk_copy_g2s(s_hid, P.helem_id + H.helem_off, H.helem_bytes, s_bar);
+      }
+      if constexpr (STAGE) {
+        // one 832-byte record per halo element (16-byte aligned at both ends)
+        __syncwarp();
+        for (int h = threadIdx.x; h < H.n_helem; h += 32) {
+          const int64_t id = P.helem_id[H.helem_off + h];
+          bulk_copy_g2s(s_recs + (size_t)h * kRowsRecSmem, rec + id * kRecStride, 4u * kRecStride, s_bar);
+        }
+      }
+    }
+    const int32_t* lnodes = P.lnodes + H.lnode_off;
+    for (int t = threadIdx.x; t < H.n_owned * D; t += blockDim.x)
+      s_rs[t] = P.row_ptr[(int64_t)D * lnodes[t / D] + t % D];
+    const bool landed = mbar_wait_bounded(s_bar, parity);
+    if (__syncthreads_or(!landed)) {
+      // the copy did not land within the bound: report, wait a last bounded
+      // while for the copy in flight, and leave without touching A
+      if (threadIdx.x == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
+      mbar_wait_bounded(s_bar, parity);
+      return;
+    }
+    const R lam = (R)P.lam, mu = (R)P.mu;
+    for (int t = threadIdx.x; t < H.n_tasks; t += blockDim.x) {
+      const RowTask T = s_tasks[t];
+      const bool diag = T.flags & kTaskDiag;
+      Acc<PREC> acc[D][D];
+      Acc<PREC> bacc[D];
+#pragma unroll 1
+      for (int c = 0; c < T.nc; ++c) {
+        const int code = s_contrib[T.coff + c];
+        const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
+        const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
+        const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
+        const R* re = STAGE ? s_recs + (size_t)h * kRowsRecSmem : rec + (int64_t)s_hid[h] * kRecStride;
+        const R* ga = re + 3 * a;
+        const R* gb = re + 3 * bn;
+        R K[D][D];
+        if constexpr (OP == FEA_OP_DIFFUSION) {
+          R s = R(0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (!HEX && q >= nq) break;
+            const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
+                    x2 = ld_rec<STAGE>(ga + 24 * q + 2);
+            const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
+                    y2 = ld_rec<STAGE>(gb + 24 * q + 2);
+            s += ld_rec<STAGE>(re + kRecK + q) * (x0 * y0 + x1 * y1 + x2 * y2);
+          }
+          K[0][0] = s;
+        } else {
+          R M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (!HEX && q >= nq) break;
+            const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
+                    x2 = ld_rec<STAGE>(ga + 24 * q + 2);
+            const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
+                    y2 = ld_rec<STAGE>(gb + 24 * q + 2);
+            M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
+            M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
+            M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
+          }
+          const R tr = mu * (M[0][0] + M[1][1] + M[2][2]);
+#pragma unroll
+          for (int c1 = 0; c1 < 3; ++c1)
+#pragma unroll
+            for (int c2 = 0; c2 < 3; ++c2) K[c1][c2] = lam * M[c1][c2] + mu * M[c2][c1] + (c1 == c2 ? tr : R(0));
+        }
+        if (c == 0) {
+#pragma unroll
+          for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].set(K[c1][c2]);
+        } else {
+#pragma unroll
+          for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].add(K[c1][c2]);
+        }
+        if (diag) {
+          const int slot = HEX ? (int)kRuleHex8 : rule_slot_of(type, P.tet_nq);
+          R rb = R(0);
+          for (int q = 0; q < nq; ++q) {
+            R Nqa;
+            if constexpr (PREC == FEA_FP64)
+              Nqa = P.Ntab64[slot][q][a];
+            else
+              Nqa = P.Ntab[slot][q][a];
+            rb += ld_rec<STAGE>(re + kRecW + q) * Nqa;
+          }
+          if constexpr (OP == FEA_OP_DIFFUSION)
+            bacc[0].add(rb * (R)P.src);
+          else
+#pragma unroll
+            for (int c1 = 0; c1 < 3; ++c1) bacc[c1].add(rb * (R)P.f[c1]);
+        }
+      }
+      // the entry block, rounded once, to row i and transposed to row j
+      double v[D][D];
+#pragma unroll
+      for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
+#pragma unroll
+      for (int c1 = 0; c1 < D; ++c1) {
+        const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) P.A[base + c2] = v[c1][c2];
+      }
+      if (T.flags & kTaskTranspose) {
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) {
+          const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
+#pragma unroll
+          for (int c1 = 0; c1 < D; ++c1) P.A[base + c1] = v[c1][c2];
+        }
+      }
+      if (diag) {
+        const int64_t gi = lnodes[T.li];
+#pragma unroll
+        for (int c1 = 0; c1 < D; ++c1) P.b[D * gi + c1] = bacc[c1].value();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
+                  cudaStream_t s, int* launched) {
+  const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
+  RowsPlan* plan = nullptr;
+  int rc = ensure_rows_plan(m, D, op->precision, s, &plan);
+  if (rc) return rc;
+  const RowsPlan& RP = *plan;
+  void* records = nullptr;
+  int geo_launches = 0;
+  rc = geometry_pass(op, m, s, &records, &geo_launches);
+  if (rc) return rc;
+  RowsArgs P;
+  std::memset(&P, 0, sizeof(P));
+  P.blocks = RP.blocks;
+  P.lnodes = RP.lnodes;
+  P.helem_type = RP.helem_type;
+  P.tasks = RP.tasks;
+  P.contrib = RP.contrib;
+  P.helem_id = RP.helem_id;
+  P.row_ptr = row_ptr;
+  P.rec = records;
+  P.A = A;
+  P.b = b;
+  P.st = m->status;
+  P.n_blocks = RP.n_blocks;
+  P.tet_nq = op->tet_rule ? 4 : 1;
+  const bool stage = op->precision != FEA_FP64;
+  P.L = rows_layout(RP, stage);
+  const double E = op->young, nu = op->poisson;
+  P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  P.mu = E / (2.0 * (1.0 + nu));
+  P.src = op->source;
+  for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
+  for (int k = 0; k < kNumRules; ++k) {
+    const RefRule& rr = host_rule(k);
+    for (int q = 0; q < 8; ++q)
+      for (int a = 0; a < 8; ++a) {
+        P.Ntab[k][q][a] = rr.Nf[q][a];
+        P.Ntab64[k][q][a] = rr.N[q][a];
+      }
+  }
+  const size_t smem = P.L.total;
+  if (smem > kRowsMaxSmem)
+    return fail(FEA_ERR_UNSUPPORTED, "rows: a block needs " + std::to_string(smem) + " bytes of shared memory");
+  const unsigned grid = (unsigned)RP.n_blocks;
+  auto launch = [&](auto kern) -> int {
+    FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 256, smem, s>>>(P);
+    FEA_CUDA(cudaGetLastError());
+    return FEA_OK;
+  };
+  const bool hex = RP.all_hex;
+  if (op->kind == FEA_OP_DIFFUSION) {
+    if (op->precision == FEA_FP64)
+      rc = hex ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP64, true, false>)
+               : launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP64, false, false>);
+    else
+      rc = hex ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, true, true>)
+               : launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, false, true>);
+  } else {
+    if (op->precision == FEA_FP64)
+      rc = hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP64, true, false>)
+               : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP64, false, false>);
+    else
+      rc = hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, true, true>)
+               : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, false, true>);
+  }
+  if (rc == FEA_OK) *launched = geo_launches + 1;
+  return rc;
+}
+
+}  // namespace fea
