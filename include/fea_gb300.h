@@ -221,12 +221,23 @@ int fea_row_ptr_from_counts_noalloc(const int32_t* counts_d, int64_t n, int64_t*
  * drops the current plan; the next ROWS assembly rebuilds it.  Host call. */
 int fea_mesh_set_rows_block(fea_mesh* mesh, int block_nodes);
 
+/* Elements per block of FEA_SCATTER_BLOCK (default 64; 1..108, the blocks'
+ * geometry is staged in shared memory).  A change drops the current plan.
+ * Host call. */
+int fea_mesh_set_block_elems(fea_mesh* mesh, int block_elems);
+
 /* Statistics of the current FEA_SCATTER_ROWS plan (zeros if none):
  * info[0] blocks, [1] nodes per block, [2] max local nodes of a block,
  * [3] max halo elements of a block, [4] entry tasks, [5] element
  * contributions, [6] halo elements (with repeats), [7] plan bytes on the
  * device.  Host call. */
 int fea_rows_plan_info(const fea_mesh* mesh, int64_t info[8]);
+
+/* The element coloring of FEA_SCATTER_COLOR (built by the first COLOR
+ * assembly): *n_colors classes, and, if colors_h is not NULL, the class of
+ * every element (int32 [n_elems], host).  No two elements of one class share
+ * a node.  Host call; FEA_ERR_ARG if no coloring exists yet. */
+int fea_color_info(const fea_mesh* mesh, int32_t* colors_h, int* n_colors);
 
 /* Number of kernels one fea_assemble call with this operator launches on this
  * mesh (after its pattern is built).  Host call. */

@@ -176,7 +176,8 @@ struct AsmParams {
   const int32_t* tconn;     // [n][NN] packed connectivity of the group
   const int32_t* ids;       // [n] original element ids (nullptr: identity)
   const int64_t* mapoff;    // [n] node_map offsets (nullptr: id * NN^2)
-  int64_t n;
+  const int32_t* list;      // launch index -> index in the group (nullptr: identity; coloring)
+  int64_t n;                // elements of this launch
   const int64_t* row_ptr;
   const int32_t* node_map;
   double* A;
@@ -186,6 +187,14 @@ struct AsmParams {
   double lam, mu;           // elasticity
   double f[3];
 };
+
+__device__ __forceinline__ int64_t group_index(const AsmParams& P, int64_t et) {
+  return P.list ? (int64_t)P.list[et] : et;
+}
+__device__ __forceinline__ int64_t original_id(const AsmParams& P, int64_t et) {
+  const int64_t g = group_index(P, et);
+  return P.ids ? (int64_t)P.ids[g] : g;
+}
 
 template <int OP, int PREC, int NN, int NQ, int EPC>
 struct TileSmem {
@@ -315,7 +324,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
     const int le = t / NN, a = t % NN;
     const int64_t et = e0 + le;
     if (et < P.n) {
-      const int64_t node = P.tconn[et * NN + a];
+      const int64_t node = P.tconn[group_index(P, et) * NN + a];
       sm.X[le][a][0] = P.coords[3 * node + 0];
       sm.X[le][a][1] = P.coords[3 * node + 1];
       sm.X[le][a][2] = P.coords[3 * node + 2];
@@ -328,7 +337,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
     const int64_t et = e0 + le;
     if (et >= P.n) continue;
     if constexpr (PREC == FEA_FP64) {
-      geometry_fp64<OP, NN>(sm, rr, le, q, P.ids ? P.ids[et] : et, P);
+      geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
     } else {
       if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
     }
@@ -338,7 +347,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
     for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
       const int le = t / NQ, q = t % NQ;
       const int64_t et = e0 + le;
-      if (et < P.n && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, P.ids ? P.ids[et] : et, P);
+      if (et < P.n && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
     }
   }
   __syncthreads();
@@ -407,10 +416,21 @@ __device__ __forceinline__ void row_block(const typename Cfg::Smem& sm, const Re
 __device__ __forceinline__ double widen(float x) { return f32_to_f64_exact(x); }
 __device__ __forceinline__ double widen(double x) { return x; }
 
-// ATOMIC scatter: FP64 atomic adds of each row block (Alg. "no coloring")
-template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
-__global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__ RefRule rr,
-                                                         const __grid_constant__ AsmParams P) {
+// add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain
+// read-modify-write when no other element of the launch touches the entry
+// (COLOR: the launch holds one color class, Alg. "coloring")
+template <int SC>
+__device__ __forceinline__ void scatter_add(double* p, double v) {
+  if constexpr (SC == FEA_SCATTER_ATOMIC)
+    atomicAdd(p, v);
+  else
+    *p += v;
+}
+
+// Tile kernel: integrate EPC elements, scatter each row block (a, b0..b0+NB)
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
+__global__ void __launch_bounds__(128) k_assemble_tile(const __grid_constant__ RefRule rr,
+                                                       const __grid_constant__ AsmParams P) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   using R = typename Cfg::R;
   constexpr int NN = Cfg::NN, D = Cfg::D, NB = Cfg::NB, LPE = Cfg::LPE, EPW = Cfg::EPW;
@@ -430,9 +450,10 @@ __global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__
   R K[NB][D][D], rhs[D];
   row_block<Cfg, OP>(sm, rr, P, le, a, b0, K, rhs);
 
-  const int64_t node = P.tconn[et * NN + a];
-  const int64_t id = P.ids ? (int64_t)P.ids[et] : et;
-  const int64_t moff = P.mapoff ? P.mapoff[et] : id * NN * NN;
+  const int64_t g = group_index(P, et);
+  const int64_t node = P.tconn[g * NN + a];
+  const int64_t id = P.ids ? (int64_t)P.ids[g] : g;
+  const int64_t moff = P.mapoff ? P.mapoff[g] : id * NN * NN;
   const int32_t* mp = P.node_map + moff + a * NN + b0;
   int64_t rb[D];
 #pragma unroll
@@ -443,40 +464,46 @@ __global__ void __launch_bounds__(128) k_assemble_atomic(const __grid_constant__
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int cc = 0; cc < D; ++cc) atomicAdd(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
+      for (int cc = 0; cc < D; ++cc) scatter_add<SC>(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
   }
   if (b0 == 0)
 #pragma unroll
-    for (int c = 0; c < D; ++c) atomicAdd(P.b + D * node + c, widen(rhs[c]));
+    for (int c = 0; c < D; ++c) scatter_add<SC>(P.b + D * node + c, widen(rhs[c]));
 }
 
 // ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
-template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
-static int launch_atomic(const AsmParams& P, cudaStream_t s) {
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
+static int launch_tile(const AsmParams& P, cudaStream_t s) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   const unsigned grid = grid_for(P.n, Cfg::EPC);
-  k_assemble_atomic<TYPE, SLOT, OP, PREC, SPLIT><<<grid, Cfg::THREADS, 0, s>>>(host_rule(SLOT), P);
+  k_assemble_tile<TYPE, SLOT, OP, PREC, SPLIT, SC><<<grid, Cfg::THREADS, 0, s>>>(host_rule(SLOT), P);
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }
 
-template <int OP, int PREC>
-static int launch_group(int type, int tet_rule, const AsmParams& P, cudaStream_t s) {
+template <int OP, int PREC, int SC>
+static int launch_group_sc(int type, int tet_rule, const AsmParams& P, cudaStream_t s) {
   // FP64 elasticity splits the columns of hex8 / prism6 over two lanes (register budget)
   constexpr int S2 = (OP == FEA_OP_ELASTICITY && PREC == FEA_FP64) ? 2 : 1;
   switch (type) {
     case FEA_TET4:
-      return tet_rule ? launch_atomic<FEA_TET4, kRuleTet4, OP, PREC, 1>(P, s)
-                      : launch_atomic<FEA_TET4, kRuleTet1, OP, PREC, 1>(P, s);
+      return tet_rule ? launch_tile<FEA_TET4, kRuleTet4, OP, PREC, 1, SC>(P, s)
+                      : launch_tile<FEA_TET4, kRuleTet1, OP, PREC, 1, SC>(P, s);
     case FEA_PYR5:
-      return launch_atomic<FEA_PYR5, kRulePyr8, OP, PREC, 1>(P, s);
+      return launch_tile<FEA_PYR5, kRulePyr8, OP, PREC, 1, SC>(P, s);
     case FEA_PRISM6:
-      return launch_atomic<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(P, s);
+      return launch_tile<FEA_PRISM6, kRulePrism6, OP, PREC, S2, SC>(P, s);
     default:
-      return launch_atomic<FEA_HEX8, kRuleHex8, OP, PREC, S2>(P, s);
+      return launch_tile<FEA_HEX8, kRuleHex8, OP, PREC, S2, SC>(P, s);
   }
+}
+
+template <int OP, int PREC>
+static int launch_group(int type, int tet_rule, const AsmParams& P, cudaStream_t s) {
+  return P.list ? launch_group_sc<OP, PREC, FEA_SCATTER_COLOR>(type, tet_rule, P, s)
+                : launch_group_sc<OP, PREC, FEA_SCATTER_ATOMIC>(type, tet_rule, P, s);
 }
 
 int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
@@ -486,8 +513,8 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
   if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
-  if (op->scatter != FEA_SCATTER_ATOMIC && op->scatter != FEA_SCATTER_ROWS)
-    return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: scatter variant not available");
+  if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_ROWS)
+    return fail(FEA_ERR_ARG, "fea_assemble: unknown scatter variant");
   if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
   const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
   if (m->pattern_ndof != D || !m->pattern_built)
@@ -513,10 +540,30 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));  // all kernels are done here
     return FEA_OK;
   }
+  if (op->scatter == FEA_SCATTER_COLOR && !m->color) {
+    int rc = build_color_plan(m, s);  // host-synchronous, first call only
+    if (rc) return rc;
+  }
+  RowsPlan* bplan = nullptr;
+  if (op->scatter == FEA_SCATTER_BLOCK) {
+    int rc = ensure_blocks_plan(m, D, s, &bplan);  // host work on the first call only
+    if (rc) return rc;
+  }
   if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
   FEA_CUDA(cudaMemsetAsync(A, 0, nnz * sizeof(double), s));
   FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
   if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+  if (op->scatter == FEA_SCATTER_BLOCK) {
+    // geometry records, then one CTA per element block: interior entries are
+    // stored, block-boundary entries added atomically into the zeroed A and b
+    void* records = nullptr;
+    int rc = geometry_pass(op, m, s, &records, nullptr);
+    if (rc) return rc;
+    rc = launch_task_kernel(op, *bplan, records, row_ptr, A, b, m->status, s);
+    if (rc) return rc;
+    for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
+    return FEA_OK;
+  }
   int launched = 0;
 
   AsmParams P;
@@ -534,13 +581,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   P.mu = E / (2.0 * (1.0 + nu));
   for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
-  for (int t = 0; t < kNumTypes; ++t) {
-    const TypeGroup& g = m->group[t];
-    if (!g.n) continue;
-    P.tconn = g.conn;
-    P.ids = g.ids;
-    P.mapoff = g.mapoff;
-    P.n = g.n;
+  auto run = [&](int t) -> int {
     int rc;
     if (op->kind == FEA_OP_DIFFUSION)
       rc = op->precision == FEA_FP64 ? launch_group<FEA_OP_DIFFUSION, FEA_FP64>(t, op->tet_rule, P, s)
@@ -551,14 +592,51 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     if (rc) return rc;
     if (2 + launched < nev) FEA_CUDA(cudaEventRecord(ev[2 + launched], s));
     ++launched;
+    return FEA_OK;
+  };
+  if (op->scatter == FEA_SCATTER_COLOR) {
+    // one launch per (color, element type): a launch never holds two elements
+    // sharing a node, so its adds are plain read-modify-writes
+    const ColorPlan& C = *m->color;
+    for (int c = 0; c < C.n_colors; ++c)
+      for (int t = 0; t < kNumTypes; ++t) {
+        const size_t k = (size_t)c * kNumTypes + t;
+        const int64_t n = C.seg_off[k + 1] - C.seg_off[k];
+        if (!n) continue;
+        const TypeGroup& g = m->group[t];
+        P.tconn = g.conn;
+        P.ids = g.ids;
+        P.mapoff = g.mapoff;
+        P.list = C.lists + C.seg_off[k];
+        P.n = n;
+        int rc = run(t);
+        if (rc) return rc;
+      }
+    return FEA_OK;
+  }
+  for (int t = 0; t < kNumTypes; ++t) {
+    const TypeGroup& g = m->group[t];
+    if (!g.n) continue;
+    P.tconn = g.conn;
+    P.ids = g.ids;
+    P.mapoff = g.mapoff;
+    P.list = nullptr;
+    P.n = g.n;
+    int rc = run(t);
+    if (rc) return rc;
   }
   return FEA_OK;
 }
 
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
   if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
-  if (op->scatter == FEA_SCATTER_ROWS) {
-    *n = geometry_launches(m) + 1;  // geometry pass per element type, then the row kernel
+  if (op->scatter == FEA_SCATTER_ROWS || op->scatter == FEA_SCATTER_BLOCK) {
+    *n = geometry_launches(m) + 1;  // geometry pass per element type, then the task kernel
+    return FEA_OK;
+  }
+  if (op->scatter == FEA_SCATTER_COLOR) {
+    if (!m->color) return fail(FEA_ERR_ARG, "fea_assemble_launches: the coloring is built by the first COLOR call");
+    *n = color_launches(m);
     return FEA_OK;
   }
   int k = 0;

@@ -55,6 +55,11 @@ static void free_mesh(fea_mesh* m) {
   drop_rows_plans(m);
   cudaFree(m->geo[0]);
   cudaFree(m->geo[1]);
+  free_color_plan(m);
+  if (m->blocks) {
+    free_rows_plan(m->blocks);
+    delete m->blocks;
+  }
   delete m;
 }
 
@@ -261,6 +266,20 @@ int fea_mesh_set_rows_block(fea_mesh* m, int block_nodes) {
   return FEA_OK;
 }
 
+int fea_mesh_set_block_elems(fea_mesh* m, int block_elems) {
+  if (!m) return fail(FEA_ERR_ARG, "fea_mesh_set_block_elems: null handle");
+  if (block_elems < 1 || block_elems > kRowsStageHalo)
+    return fail(FEA_ERR_ARG, "fea_mesh_set_block_elems: elements per block in [1, " + std::to_string(kRowsStageHalo) + "]");
+  if (block_elems != m->block_elems && m->blocks) {
+    cudaDeviceSynchronize();
+    free_rows_plan(m->blocks);
+    delete m->blocks;
+    m->blocks = nullptr;
+  }
+  m->block_elems = block_elems;
+  return FEA_OK;
+}
+
 int fea_rows_plan_info(const fea_mesh* m, int64_t info[8]) {
   if (!m || !info) return fail(FEA_ERR_ARG, "fea_rows_plan_info: null argument");
   for (int k = 0; k < 8; ++k) info[k] = 0;
@@ -275,6 +294,14 @@ int fea_rows_plan_info(const fea_mesh* m, int64_t info[8]) {
   info[5] = P.n_contrib;
   info[6] = P.n_helem_total;
   info[7] = (int64_t)P.bytes;
+  return FEA_OK;
+}
+
+int fea_color_info(const fea_mesh* m, int32_t* colors_h, int* n_colors) {
+  if (!m || !n_colors) return fail(FEA_ERR_ARG, "fea_color_info: null argument");
+  if (!m->color) return fail(FEA_ERR_ARG, "fea_color_info: no coloring yet (run a FEA_SCATTER_COLOR assembly)");
+  *n_colors = m->color->n_colors;
+  if (colors_h) std::memcpy(colors_h, m->color->colors_host.data(), m->n_elems * sizeof(int32_t));
   return FEA_OK;
 }
 

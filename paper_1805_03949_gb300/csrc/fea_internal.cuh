@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fea_gb300.h"
 #include "geometry.cuh"
@@ -31,6 +32,14 @@ __device__ __forceinline__ void latch_error(DevStatus* st, int code, unsigned lo
   atomicCAS(&st->code, 0, code);
   atomicMin(&st->info, id);
 }
+
+// Element coloring (color.cu): group-local element indices per (color, type).
+struct ColorPlan {
+  int n_colors = 0;
+  std::vector<int64_t> seg_off;      // [n_colors * 4 + 1] offsets of the (color, type) segments in lists
+  int32_t* lists = nullptr;          // device
+  std::vector<int32_t> colors_host;  // color of every element (original ids)
+};
 
 // Per-type element group: original ids and packed connectivity.
 struct TypeGroup {
@@ -67,6 +76,9 @@ struct fea_mesh {
   // owner-computes row assembly (FEA_SCATTER_ROWS)
   fea::RowsPlan* rows[2] = {nullptr, nullptr};  // per precision (FEA_FP64, FEA_FP32_INTEGRATE)
   void* geo[2] = {nullptr, nullptr};            // geometry records per precision (geometry.cu)
+  fea::ColorPlan* color = nullptr;              // FEA_SCATTER_COLOR classes (color.cu)
+  fea::RowsPlan* blocks = nullptr;              // FEA_SCATTER_BLOCK plan (blocks.cu)
+  int block_elems = 64;                         // elements per block of FEA_SCATTER_BLOCK
   int rows_block_nodes = 64;
 };
 
@@ -98,5 +110,10 @@ int exclusive_scan_i32(const int32_t* in, int64_t n, int64_t* out, cudaStream_t 
 int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
              double* A, double* b, cudaStream_t s);
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n);
+
+// color.cu
+int build_color_plan(fea_mesh* m, cudaStream_t s);
+void free_color_plan(fea_mesh* m);
+int color_launches(const fea_mesh* m);
 
 }  // namespace fea

@@ -56,16 +56,6 @@ static inline uint32_t spread_bits10(uint32_t v) {
   return v;
 }
 
-struct HostBlock {
-  std::vector<int32_t> lnodes;     // owned first
-  std::vector<int32_t> helem;      // original element ids
-  std::vector<uint8_t> htype;
-  std::vector<uint16_t> hln;       // [helem][8]
-  std::vector<RowTask> tasks;
-  std::vector<uint16_t> contrib;
-  int n_owned = 0;
-};
-
 static int type_of_nn(int nn) { return nn == 4 ? FEA_TET4 : nn == 5 ? FEA_PYR5 : nn == 6 ? FEA_PRISM6 : FEA_HEX8; }
 
 int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaStream_t s, RowsPlan** out) {
@@ -248,12 +238,18 @@ int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaSt
   for (auto& e : errors)
     if (!e.empty()) return fail(FEA_ERR_UNSUPPORTED, e);
 
-  // flatten
+  return upload_plan(blocks, ndof, block_nodes, halo_cap, m->uniform && m->uniform_type == FEA_HEX8, out);
+}
+
+// Concatenate the per-block lists (16-byte padded) and copy them to the device.
+int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int halo_cap, bool all_hex,
+                RowsPlan** out) {
+  const int64_t nb = (int64_t)blocks.size();
   RowsPlan P;
   P.ndof = ndof;
   P.block_nodes = block_nodes;
   P.halo_cap = halo_cap;
-  P.all_hex = m->uniform && m->uniform_type == FEA_HEX8;
+  P.all_hex = all_hex;
   P.n_blocks = nb;
   std::vector<RowBlock> hdr(nb);
   int64_t nl = 0, nh = 0, nt = 0, nc = 0;

@@ -5,10 +5,13 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <vector>
 
 #include "fea_gb300.h"
 
 namespace fea {
+
+struct DevStatus;
 
 constexpr int kRowsMaxHalo = 1024;            // halo elements per block (10-bit index in a contributor)
 constexpr int kRowsMaxOwned = 255;            // owned nodes per block (8-bit index in a task)
@@ -19,6 +22,8 @@ constexpr int kRowsQStride = 9;               // values per halo element in the 
 constexpr int kRowsDStride = 23;              // FP32 relative coordinates per halo element (7 x 3 + x_0 + pad)
 constexpr uint8_t kTaskDiag = 1;              // entry (i, i): also accumulates b_i
 constexpr uint8_t kTaskTranspose = 2;         // j is owned too: write the transposed block to row j
+constexpr uint8_t kTaskAtomicA = 4;           // block-task: elements outside the block add to (i, j) too
+constexpr uint8_t kTaskAtomicB = 8;           // block-task: elements outside the block add to b_i too
 
 // One entry block (i, j) of an owned row i: node j sits at slot k of row i
 // (and i at slot kt of row j when the transpose is written).  Its element
@@ -63,7 +68,24 @@ struct RowsPlan {
   uint16_t* contrib = nullptr;
 };
 
+// host-side lists of one block while a plan is built
+struct HostBlock {
+  std::vector<int32_t> lnodes;     // rows first (owned nodes), then the other local nodes
+  std::vector<int32_t> helem;      // original element ids
+  std::vector<uint8_t> htype;
+  std::vector<uint16_t> hln;       // [helem][8]
+  std::vector<RowTask> tasks;
+  std::vector<uint16_t> contrib;
+  int n_owned = 0;
+};
+
+int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int halo_cap, bool all_hex,
+                RowsPlan** out);
 int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaStream_t s, RowsPlan** out);
+// Block-task plan (FEA_SCATTER_BLOCK): blocks of at most block_elems elements
+// along a Morton curve of the element centroids; every entry touched by a
+// block is one task, flagged atomic when elements outside the block add to it.
+int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, RowsPlan** out);
 // the plan for (ndof, precision), built on first use with a halo cap that lets
 // two CTAs share an SM; if a block still does not fit, the node cap is halved
 int ensure_rows_plan(fea_mesh* m, int ndof, int precision, cudaStream_t s, RowsPlan** out);
@@ -72,5 +94,10 @@ void free_rows_plan(RowsPlan* P);
 RowsLayout rows_layout(const RowsPlan& P, bool stage);
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
                   cudaStream_t s, int* launched);
+// the block-task plan of a mesh, built on first use
+int ensure_blocks_plan(fea_mesh* m, int ndof, cudaStream_t s, RowsPlan** out);
+// launch the task kernel of a plan (ROWS or BLOCK) on precomputed geometry records
+int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* records, const int64_t* row_ptr,
+                       double* A, double* b, DevStatus* st, cudaStream_t s);
 
 }  // namespace fea

@@ -247,24 +247,42 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
       for (int c1 = 0; c1 < D; ++c1)
 #pragma unroll
         for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
+      // complete entries are stored; block-boundary entries (block-task plan)
+      // are added to A with FP64 atomics
+      const bool at = T.flags & kTaskAtomicA;
 #pragma unroll
       for (int c1 = 0; c1 < D; ++c1) {
         const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
 #pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) P.A[base + c2] = v[c1][c2];
+        for (int c2 = 0; c2 < D; ++c2) {
+          if (at)
+            atomicAdd(P.A + base + c2, v[c1][c2]);
+          else
+            P.A[base + c2] = v[c1][c2];
+        }
       }
       if (T.flags & kTaskTranspose) {
 #pragma unroll
         for (int c2 = 0; c2 < D; ++c2) {
           const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
 #pragma unroll
-          for (int c1 = 0; c1 < D; ++c1) P.A[base + c1] = v[c1][c2];
+          for (int c1 = 0; c1 < D; ++c1) {
+            if (at)
+              atomicAdd(P.A + base + c1, v[c1][c2]);
+            else
+              P.A[base + c1] = v[c1][c2];
+          }
         }
       }
       if (diag) {
         const int64_t gi = lnodes[T.li];
 #pragma unroll
-        for (int c1 = 0; c1 < D; ++c1) P.b[D * gi + c1] = bacc[c1].value();
+        for (int c1 = 0; c1 < D; ++c1) {
+          if (T.flags & kTaskAtomicB)
+            atomicAdd(P.b + D * gi + c1, bacc[c1].value());
+          else
+            P.b[D * gi + c1] = bacc[c1].value();
+        }
       }
     }
     __syncthreads();
@@ -277,11 +295,18 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
   RowsPlan* plan = nullptr;
   int rc = ensure_rows_plan(m, D, op->precision, s, &plan);
   if (rc) return rc;
-  const RowsPlan& RP = *plan;
   void* records = nullptr;
   int geo_launches = 0;
   rc = geometry_pass(op, m, s, &records, &geo_launches);
   if (rc) return rc;
+  rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s);
+  if (rc == FEA_OK) *launched = geo_launches + 1;
+  return rc;
+}
+
+int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* records, const int64_t* row_ptr,
+                       double* A, double* b, DevStatus* st, cudaStream_t s) {
+  int rc = FEA_OK;
   RowsArgs P;
   std::memset(&P, 0, sizeof(P));
   P.blocks = RP.blocks;
@@ -294,7 +319,7 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
   P.rec = records;
   P.A = A;
   P.b = b;
-  P.st = m->status;
+  P.st = st;
   P.n_blocks = RP.n_blocks;
   P.tet_nq = op->tet_rule ? 4 : 1;
   const bool stage = op->precision != FEA_FP64;
@@ -338,7 +363,6 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
       rc = hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, true, true>)
                : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, false, true>);
   }
-  if (rc == FEA_OK) *launched = geo_launches + 1;
   return rc;
 }
 

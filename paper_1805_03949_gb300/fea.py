@@ -75,6 +75,8 @@ def _load():
         "fea_row_ptr_from_counts_noalloc": (I32, [P, I64, P, P]),
         "fea_mesh_set_rows_block": (I32, [P, I32]),
         "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
+        "fea_color_info": (I32, [P, P, ctypes.POINTER(I32)]),
+        "fea_mesh_set_block_elems": (I32, [P, I32]),
     }
     for name, (rt, at) in sig.items():
         f = getattr(lib, name)
@@ -196,11 +198,23 @@ def fea_mesh_set_rows_block(h, block_nodes: int):
     _check(_lib.fea_mesh_set_rows_block(h, int(block_nodes)))
 
 
+def fea_mesh_set_block_elems(h, block_elems: int):
+    _check(_lib.fea_mesh_set_block_elems(h, int(block_elems)))
+
+
 def fea_rows_plan_info(h) -> dict:
     arr = (ctypes.c_int64 * 8)()
     _check(_lib.fea_rows_plan_info(h, arr))
     keys = ["blocks", "block_nodes", "max_local", "max_halo", "tasks", "contributions", "halo_elements", "bytes"]
     return dict(zip(keys, list(arr)))
+
+
+def fea_color_info(h, n_elems: int):
+    """(n_colors, int32 numpy array of every element's color class)."""
+    n = ctypes.c_int()
+    colors = np.zeros(n_elems, dtype=np.int32)
+    _check(_lib.fea_color_info(h, ctypes.c_void_p(colors.ctypes.data), ctypes.byref(n)))
+    return n.value, colors
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:

@@ -60,7 +60,7 @@ CASES = {
 }
 
 
-SCATTERS = {"atomic": 0, "rows": 3}
+SCATTERS = {"atomic": 0, "color": 1, "block": 2, "rows": 3}
 
 
 def _run_case(fea, oracle, name, precision, scatter=0, block_nodes=None):
@@ -168,5 +168,28 @@ def test_rows_is_deterministic_and_symmetric():
         assert exact < M.nnz // 2                     # most entries are computed once for both triangles
         info = fea.fea_rows_plan_info(s.handle)
         assert info["blocks"] >= -(-mesh.n_nodes // 64) and info["tasks"] > 0
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["hybrid6_diffusion", "hex10_elasticity", "kuhn16_poisson"])
+def test_coloring_is_valid(name):
+    """No two elements of one color class share a node (Alg. "coloring")."""
+    fea = engine()
+    factory, kind, _, tet_rule, params = CASES[name]
+    mesh = factory()
+    s = fea.System.from_mesh(mesh, 1 if kind == 0 else 3)
+    try:
+        s.assemble(fea.make_operator(kind=kind, scatter=fea.FEA_SCATTER_COLOR, tet_rule=tet_rule, **params))
+        s.check()
+        n_colors, colors = fea.fea_color_info(s.handle, mesh.n_elems)
+        assert colors.min() == 0 and colors.max() == n_colors - 1
+        seen = {}
+        for e in range(mesh.n_elems):
+            for node in mesh.element_nodes(e):
+                key = (int(node), int(colors[e]))
+                assert key not in seen, (e, seen.get(key))
+                seen[key] = e
+        assert fea.fea_assemble_launches(fea.make_operator(kind=kind, scatter=1), s.handle) >= n_colors
     finally:
         s.close()

@@ -82,7 +82,7 @@ def test_c2_pattern_closed_form(c2):
                 assert col[rp[3 * i] + 3 * nmap[e, a, bb]] == 3 * conn[e, bb]
 
 
-@pytest.mark.parametrize("scatter", [3, 0])
+@pytest.mark.parametrize("scatter", [3, 0, 1, 2])
 @pytest.mark.parametrize("precision", [1, 0])
 def test_c2_sampled_rows(oracle, c2, precision, scatter):
     fea, mesh, s = c2
@@ -106,7 +106,7 @@ def test_c3_hybrid_sampled_rows(oracle):
         rng = np.random.default_rng(3)
         nodes = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, size=24), [0, mesh.n_nodes - 1]]))
         nodes = nodes.astype(np.int32)
-        for precision, tol, scatter in ((1, FP32_TOL, 3), (0, FP64_TOL, 3), (1, FP32_TOL, 0)):
+        for precision, tol, scatter in ((1, FP32_TOL, 3), (0, FP64_TOL, 3), (1, FP32_TOL, 0), (1, FP32_TOL, 2)):
             s.A.fill_(float("nan"))
             s.assemble(fea.make_operator(kind=0, precision=precision, scatter=scatter, tet_rule=1, k0=1.0, k2=1.0,
                                          source=1.0))
