@@ -534,10 +534,14 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
     FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
     if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
-    int launched = 0;
-    int rc = assemble_rows(op, m, row_ptr, A, b, s, &launched);
+    void* records = nullptr;
+    int geo = 0;
+    int rc = geometry_pass(op, m, s, &records, &geo);
     if (rc) return rc;
-    for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));  // all kernels are done here
+    for (int k = 2; k < 2 + geo && k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
+    rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s);
+    if (rc) return rc;
+    for (int k = 2 + geo; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     return FEA_OK;
   }
   if (op->scatter == FEA_SCATTER_COLOR && !m->color) {
@@ -557,11 +561,13 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     // geometry records, then one CTA per element block: interior entries are
     // stored, block-boundary entries added atomically into the zeroed A and b
     void* records = nullptr;
-    int rc = geometry_pass(op, m, s, &records, nullptr);
+    int geo = 0;
+    int rc = geometry_pass(op, m, s, &records, &geo);
     if (rc) return rc;
+    for (int k = 2; k < 2 + geo && k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     rc = launch_task_kernel(op, *bplan, records, row_ptr, A, b, m->status, s);
     if (rc) return rc;
-    for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
+    for (int k = 2 + geo; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     return FEA_OK;
   }
   int launched = 0;
