@@ -66,11 +66,17 @@ typedef enum {
 } fea_op_kind;
 
 typedef enum {
-  FEA_FP64 = 0,          /* geometry, integration and accumulation in FP64 */
-  FEA_FP32_INTEGRATE = 1 /* element integration in FP32, accumulation into A and b in FP64;
-                            Jacobian, determinant and inverse in FP64 for distorted elements
-                            (Frobenius condition number of J above FEA_KAPPA_FP64 at some
-                            quadrature point, or det J near zero), FP32 otherwise */
+  FEA_FP64 = 0,           /* geometry, integration and accumulation in FP64 */
+  FEA_FP32_INTEGRATE = 1, /* element integration in FP32, accumulation into A and b in FP64;
+                             J, its cofactors and det J in FP64 for every element (every
+                             non-affine element counts as distorted); J^{-1} = C^T / det J and
+                             the physical gradients are formed in FP32 from the rounded FP64
+                             cofactors and determinant */
+  FEA_FP32_ADAPTIVE = 2   /* as FEA_FP32_INTEGRATE, but the geometry is FP32 (on node
+                             coordinates relative to node 0, subtracted in FP64) unless the
+                             element is distorted: Frobenius condition number of J above
+                             FEA_KAPPA_FP64 at some quadrature point, or a det J FP32 cannot
+                             trust; such elements are redone in FP64 */
 } fea_precision;
 
 #define FEA_KAPPA_FP64 12.0

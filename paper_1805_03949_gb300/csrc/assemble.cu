@@ -186,6 +186,7 @@ struct AsmParams {
   double k0, k2, src;       // diffusion
   double lam, mu;           // elasticity
   double f[3];
+  int geo64;                // FP32 tiles: 1 = FP64 geometry for every element, 0 = adaptive
 };
 
 __device__ __forceinline__ int64_t group_index(const AsmParams& P, int64_t et) {
@@ -206,11 +207,59 @@ struct TileSmem {
   int flag[EPC];            // FP32 mode: element is distorted -> FP64 geometry
 };
 
-// FP64 geometry of point q of element le; results rounded to the tile type R.
+// Tile values of point q from the FP64 Jacobian J' = s J (s a power of two):
+// det J = det'/s^3, grad N_a = J^{-T} grad_xi N_a = s C' grad_xi N_a / det'.
+// FP64 tiles keep FP64; FP32 tiles round the cofactors and the determinant
+// once and form the gradients in FP32.
+template <int OP, int NN, typename Smem>
+__device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
+                                                double (&J)[3][3], double s, double xq, const AsmParams& P) {
+  using R = std::remove_reference_t<decltype(sm.G[0][0][0][0])>;
+  double C[3][3];
+  cofactors(J, C);
+  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
+  const double wd = rr.w[q] * det * (1.0 / (s * s * s));
+  if constexpr (std::is_same<R, double>::value) {
+    const double inv = s / det;
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        // g_a,i = sum_j dN_a/dxi_j (J^{-1})_{j i},  (J^{-1})_{j i} = C_{i j} / det
+        sm.G[le][q][a][i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+    sm.W[le][q] = wd;
+    if constexpr (OP == FEA_OP_DIFFUSION)
+      sm.S[le][q] = wd * (P.k0 + P.k2 * xq * xq);
+    else
+      sm.S[le][q] = wd;
+  } else {
+    float Cf[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Cf[i][j] = (float)C[i][j];
+    const float inv = (float)s / (float)det;
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        sm.G[le][q][a][i] = (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * inv;
+    const float wdf = (float)wd;
+    sm.W[le][q] = wdf;
+    if constexpr (OP == FEA_OP_DIFFUSION) {
+      const float x = (float)xq;
+      sm.S[le][q] = wdf * ((float)P.k0 + (float)P.k2 * x * x);
+    } else {
+      sm.S[le][q] = wdf;
+    }
+  }
+}
+
+// FP64 geometry of point q of element le, J from the node coordinates
 template <int OP, int NN, typename Smem>
 __device__ __forceinline__ void geometry_fp64(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
                                               const AsmParams& P) {
-  using R = std::remove_reference_t<decltype(sm.G[0][0][0][0])>;
   double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double xq = sm.X[le][0][0];
 #pragma unroll
@@ -226,26 +275,7 @@ __device__ __forceinline__ void geometry_fp64(Smem& sm, const RefRule& rr, int l
       J[2][j] += d2 * rr.dN[q][a][j];
     }
   }
-  double C[3][3];
-  cofactors(J, C);
-  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-  if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
-  const double inv = 1.0 / det;
-#pragma unroll
-  for (int a = 0; a < NN; ++a) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      // g_a,i = sum_j dN_a/dxi_j (J^{-1})_{j i},  (J^{-1})_{j i} = C_{i j} / det
-      const double v = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
-      sm.G[le][q][a][i] = (R)v;
-    }
-  }
-  const double wd = rr.w[q] * det;
-  sm.W[le][q] = (R)wd;
-  if constexpr (OP == FEA_OP_DIFFUSION)
-    sm.S[le][q] = (R)(wd * (P.k0 + P.k2 * xq * xq));
-  else
-    sm.S[le][q] = (R)wd;
+  geometry_finish<OP, NN>(sm, rr, le, q, elem_id, J, 1.0, xq, P);
 }
 
 // FP32 geometry on coordinates relative to node 0; returns false when the
@@ -310,7 +340,9 @@ struct TileCfg {
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int EPC = EPW * WARPS;       // elements per CTA
   static constexpr int NB = NN / SPLIT;         // columns per lane
+  static constexpr bool kModal = TYPE == FEA_HEX8 && SLOT == kRuleHex8;
   static_assert(NN % SPLIT == 0, "SPLIT must divide the node count");
+  static_assert(!kModal || (EPC * 8 % 32 == 0 && EPC * 8 <= THREADS), "modal hex geometry needs whole warps");
   using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
   using Smem = TileSmem<OP, PREC, NN, NQ, EPC>;
 };
@@ -320,6 +352,7 @@ template <class Cfg, int OP, int PREC>
 __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefRule& rr, const AsmParams& P,
                                               int64_t e0) {
   constexpr int NN = Cfg::NN, NQ = Cfg::NQ, EPC = Cfg::EPC;
+  constexpr bool kModal = Cfg::kModal;
   for (int t = threadIdx.x; t < EPC * NN; t += Cfg::THREADS) {
     const int le = t / NN, a = t % NN;
     const int64_t et = e0 + le;
@@ -332,17 +365,57 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
   }
   if (threadIdx.x < EPC) sm.flag[threadIdx.x] = 0;
   __syncthreads();
+  const bool all64 = PREC == FEA_FP64 || P.geo64;  // uniform over the grid
+  if constexpr (kModal) {
+    if (all64) {
+      // trilinear hex in modal form: one lane per (element, corner p = point q);
+      // EPC * 8 is a whole number of warps, so every lane of them takes part
+      const int t = threadIdx.x;
+      if (t < EPC * 8) {
+        const int le = t >> 3, p = t & 7;
+        const int64_t et = e0 + le;
+        const bool valid = et < P.n;
+        const int a = hex8_corner_node(p);
+        double v[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] - sm.X[le][0][i] : 0.0;
+        const double x0 = valid ? sm.X[le][0][0] : 0.0;
+        hex8_modal(v);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sm.X[le][p][i] = v[i];
+        __syncwarp();
+        if (valid) {
+          double J[3][3];
+          hex8_jacobian(sm.X[le], p, J);
+          double xq = 0.0;
+          if constexpr (OP == FEA_OP_DIFFUSION) {
+            const double g = 0.57735026918962576451;
+            const double xs = (p & 1) ? g : -g, ys = (p & 2) ? g : -g, zs = (p & 4) ? g : -g;
+            const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = fma(sm.X[le][k][0], m[k], acc);
+            xq = x0 + 0.125 * acc;
+          }
+          geometry_finish<OP, NN>(sm, rr, le, p, original_id(P, et), J, 8.0, xq, P);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
   for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
     const int le = t / NQ, q = t % NQ;
     const int64_t et = e0 + le;
     if (et >= P.n) continue;
-    if constexpr (PREC == FEA_FP64) {
+    if (all64) {
       geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
     } else {
       if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
     }
   }
-  if constexpr (PREC != FEA_FP64) {
+  if (!all64) {
     __syncthreads();
     for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
       const int le = t / NQ, q = t % NQ;
@@ -511,7 +584,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   if (!op || !m || !row_ptr || !node_map || !A || !b) return fail(FEA_ERR_ARG, "fea_assemble: null argument");
   if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
-  if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE)
+  if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE && op->precision != FEA_FP32_ADAPTIVE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
   if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_ROWS)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown scatter variant");
@@ -587,6 +660,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   P.mu = E / (2.0 * (1.0 + nu));
   for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
+  P.geo64 = op->precision != FEA_FP32_ADAPTIVE;
   auto run = [&](int t) -> int {
     int rc;
     if (op->kind == FEA_OP_DIFFUSION)

@@ -10,7 +10,11 @@
 //   A^e_ab = sum_q K(q) g^_a(q) . g^_b(q)                                  (diffusion)
 // and its right-hand side b^e_a = sum_q W(q) N_a(q) f.
 //
-// FEA_FP32_INTEGRATE: coordinates relative to node 0 are subtracted in FP64 and
+// FEA_FP32_INTEGRATE: J, its cofactors C and det J in FP64 for every element
+// (node coordinates relative to node 0; the trilinear hex in modal form, see
+// hex8_modal); C and det J are rounded to FP32 once and the gradients formed
+// from them in FP32.
+// FEA_FP32_ADAPTIVE: coordinates relative to node 0 are subtracted in FP64 and
 // rounded to FP32 once per (element, node); J, det J and J^{-1} are FP32 unless
 // the element is distorted (Frobenius condition number of J above
 // FEA_KAPPA_FP64 at some point, or a det J that FP32 cannot trust), in which
@@ -35,9 +39,57 @@ struct GeoArgs {
   DevStatus* st;
   double k0, k2;
   int diffusion;
+  int geo64;               // FP32 records: 1 = FP64 geometry for every element, 0 = adaptive
 };
 
 constexpr int kGeoThreads = 256;
+
+// Record values of point q from the FP64 Jacobian J' = s J (s a power of two):
+// det J = det'/s^3 and J^{-T} = s C'/det' with C' the cofactors of J'.
+template <int NN, int PREC>
+__device__ __forceinline__ void geo_finish(const RefRule& rr, const GeoArgs& P, int q, int64_t id, double (&J)[3][3],
+                                           double s, double xq, void* recp) {
+  double C[3][3];
+  cofactors(J, C);
+  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  if (!(det > 0.0)) {
+    latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)id);
+    return;
+  }
+  const double wd = rr.w[q] * det * (1.0 / (s * s * s));
+  if constexpr (PREC == FEA_FP64) {
+    double* rec = static_cast<double*>(recp);
+    const double sc = sqrt(wd) * s / det;
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        rec[q * 24 + 3 * a + i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * sc;
+    rec[kRecW + q] = wd;
+    if (P.diffusion) rec[kRecK + q] = P.k0 + P.k2 * xq * xq;
+  } else {
+    // J^{-1} from the FP64 cofactors and determinant, rounded once each
+    float* rec = static_cast<float*>(recp);
+    float Cf[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Cf[i][j] = (float)C[i][j];
+    const float wdf = (float)wd;
+    const float sc = sqrtf(wdf) * (float)s / (float)det;
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        rec[q * 24 + 3 * a + i] =
+            (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * sc;
+    rec[kRecW + q] = wdf;
+    if (P.diffusion) {
+      const float x = (float)xq;
+      rec[kRecK + q] = (float)P.k0 + (float)P.k2 * x * x;
+    }
+  }
+}
 
 template <int TYPE, int SLOT, int PREC>
 __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant__ RefRule rr,
@@ -46,7 +98,8 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
   constexpr int NN = nodes_of(TYPE);
   constexpr int NQ = rule_nq(SLOT);
   constexpr int EPC = kGeoThreads / 8;  // elements per CTA (8 threads each)
-  __shared__ double sX[EPC][8][3];
+  constexpr bool kModal = TYPE == FEA_HEX8 && SLOT == kRuleHex8;
+  __shared__ double sX[EPC][8][3];      // node coordinates (modal hex: then the c_k)
   __shared__ float sD[EPC][8][3];
   __shared__ int sFlag[EPC];
   const int le = threadIdx.x >> 3, lane8 = threadIdx.x & 7;
@@ -62,66 +115,99 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
   }
   if (lane8 == 0) sFlag[le] = 0;
   __syncthreads();
-  if constexpr (PREC != FEA_FP64) {
+  R* rec = reinterpret_cast<R*>(P.rec) + id * kRecStride;
+  const int q = lane8;
+  const bool all64 = PREC == FEA_FP64 || P.geo64;  // uniform over the grid
+  if (!all64) {
+    // adaptive: FP32 geometry on coordinates relative to node 0, distorted
+    // elements flagged for the FP64 redo below
     if (valid && lane8 < NN) {
       sD[le][lane8][0] = (float)(sX[le][lane8][0] - sX[le][0][0]);
       sD[le][lane8][1] = (float)(sX[le][lane8][1] - sX[le][0][1]);
       sD[le][lane8][2] = (float)(sX[le][lane8][2] - sX[le][0][2]);
     }
     __syncthreads();
-  }
-  R* rec = reinterpret_cast<R*>(P.rec) + id * kRecStride;
-  const int q = lane8;
-  bool need64 = PREC == FEA_FP64;
-  if (PREC != FEA_FP64 && valid && q < NQ) {
-    float J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    float xr = 0.0f;
+    if (valid && q < NQ) {
+      float J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      float xr = 0.0f;
 #pragma unroll
-    for (int a = 1; a < NN; ++a) {
-      const float d0 = sD[le][a][0], d1 = sD[le][a][1], d2 = sD[le][a][2];
-      xr += rr.Nf[q][a] * d0;
+      for (int a = 1; a < NN; ++a) {
+        const float d0 = sD[le][a][0], d1 = sD[le][a][1], d2 = sD[le][a][2];
+        xr += rr.Nf[q][a] * d0;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        J[0][j] += d0 * rr.dNf[q][a][j];
-        J[1][j] += d1 * rr.dNf[q][a][j];
-        J[2][j] += d2 * rr.dNf[q][a][j];
+        for (int j = 0; j < 3; ++j) {
+          J[0][j] += d0 * rr.dNf[q][a][j];
+          J[1][j] += d1 * rr.dNf[q][a][j];
+          J[2][j] += d2 * rr.dNf[q][a][j];
+        }
+      }
+      float C[3][3];
+      cofactors(J, C);
+      const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+      float nj = 0.0f, nc = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          nj += J[i][j] * J[i][j];
+          nc += C[i][j] * C[i][j];
+        }
+      const float kappa2_max = (float)(FEA_KAPPA_FP64 * FEA_KAPPA_FP64);
+      if (!(det > 0.0f) || !(nj * nc <= kappa2_max * det * det)) {
+        sFlag[le] = 1;
+      } else {
+        const float wd = rr.wf[q] * det;
+        const float sc = sqrtf(wd) / det;
+#pragma unroll
+        for (int a = 0; a < NN; ++a)
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            rec[q * 24 + 3 * a + i] =
+                (R)((rr.dNf[q][a][0] * C[i][0] + rr.dNf[q][a][1] * C[i][1] + rr.dNf[q][a][2] * C[i][2]) * sc);
+        rec[kRecW + q] = (R)wd;
+        if (P.diffusion) {
+          const float x = (float)sX[le][0][0] + xr;
+          rec[kRecK + q] = (R)((float)P.k0 + (float)P.k2 * x * x);
+        }
       }
     }
-    float C[3][3];
-    cofactors(J, C);
-    const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-    float nj = 0.0f, nc = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        nj += J[i][j] * J[i][j];
-        nc += C[i][j] * C[i][j];
-      }
-    const float kappa2_max = (float)(FEA_KAPPA_FP64 * FEA_KAPPA_FP64);
-    if (!(det > 0.0f) || !(nj * nc <= kappa2_max * det * det)) {
-      sFlag[le] = 1;
-    } else {
-      const float wd = rr.wf[q] * det;
-      const float sc = sqrtf(wd) / det;
-#pragma unroll
-      for (int a = 0; a < NN; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          rec[q * 24 + 3 * a + i] =
-              (R)((rr.dNf[q][a][0] * C[i][0] + rr.dNf[q][a][1] * C[i][1] + rr.dNf[q][a][2] * C[i][2]) * sc);
-      rec[kRecW + q] = (R)wd;
-      if (P.diffusion) {
-        const float x = (float)sX[le][0][0] + xr;
-        rec[kRecK + q] = (R)((float)P.k0 + (float)P.k2 * x * x);
-      }
-    }
-  }
-  if constexpr (PREC != FEA_FP64) {
     __syncthreads();
-    need64 = valid && sFlag[le];
   }
-  if (need64 && valid && q < NQ) {
+  if constexpr (kModal) {
+    if (all64) {
+      // every lane of the warp takes part in the butterfly (tail lanes on zeros)
+      const int p = lane8;
+      const int a = hex8_corner_node(p);
+      double v[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[i] = valid ? sX[le][a][i] - sX[le][0][i] : 0.0;
+      const double x0 = valid ? sX[le][0][0] : 0.0;
+      hex8_modal(v);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sX[le][p][i] = v[i];
+      __syncwarp();
+      if (valid) {
+        double J[3][3];
+        hex8_jacobian(sX[le], q, J);
+        double xq = 0.0;
+        if (P.diffusion) {
+          // x(xi_q) = x_0 + (1/8) sum_k c_k prod_{s in k} xi_s
+          const double g = 0.57735026918962576451;
+          const double xs = (q & 1) ? g : -g, ys = (q & 2) ? g : -g, zs = (q & 4) ? g : -g;
+          const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
+          double acc = 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc = fma(sX[le][k][0], m[k], acc);
+          xq = x0 + 0.125 * acc;
+        }
+        geo_finish<NN, PREC>(rr, P, q, id, J, 8.0, xq, rec);
+      }
+      return;
+    }
+  }
+  const bool need64 = valid && q < NQ && (all64 || sFlag[le]);
+  if (need64) {
     double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     double xq = sX[le][0][0];
 #pragma unroll
@@ -137,23 +223,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
         J[2][j] += d2 * rr.dN[q][a][j];
       }
     }
-    double C[3][3];
-    cofactors(J, C);
-    const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-    if (!(det > 0.0)) {
-      latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)id);
-    } else {
-      const double wd = rr.w[q] * det;
-      const double sc = sqrt(wd) / det;
-#pragma unroll
-      for (int a = 0; a < NN; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          rec[q * 24 + 3 * a + i] =
-              (R)((rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * sc);
-      rec[kRecW + q] = (R)wd;
-      if (P.diffusion) rec[kRecK + q] = (R)(P.k0 + P.k2 * xq * xq);
-    }
+    geo_finish<NN, PREC>(rr, P, q, id, J, 1.0, xq, rec);
   }
 }
 
@@ -194,6 +264,7 @@ int geometry_pass(const fea_operator* op, fea_mesh* m, cudaStream_t s, void** re
   P.k0 = op->k0;
   P.k2 = op->k2;
   P.diffusion = op->kind == FEA_OP_DIFFUSION;
+  P.geo64 = op->precision != FEA_FP32_ADAPTIVE;
   int k = 0;
   for (int t = 0; t < kNumTypes; ++t) {
     const TypeGroup& g = m->group[t];

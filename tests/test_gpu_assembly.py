@@ -63,6 +63,17 @@ CASES = {
 SCATTERS = {"atomic": 0, "color": 1, "block": 2, "rows": 3}
 
 
+_ORACLE_CACHE = {}
+
+
+def _reference(oracle, name, mesh):
+    """Oracle system of a case (computed once per case; every precision and scatter compares to it)."""
+    if name not in _ORACLE_CACHE:
+        _, _, oop, tet_rule, params = CASES[name]
+        _ORACLE_CACHE[name] = oracle.assemble(mesh, oop, tet_rule=tet_rule, **params)
+    return _ORACLE_CACHE[name]
+
+
 def _run_case(fea, oracle, name, precision, scatter=0, block_nodes=None):
     factory, kind, oop, tet_rule, params = CASES[name]
     mesh = factory()
@@ -75,15 +86,14 @@ def _run_case(fea, oracle, name, precision, scatter=0, block_nodes=None):
         s.A.fill_(float("nan"))                     # every entry must be written
         s.assemble(op)
         s.check()
-        ref = oracle.assemble(mesh, oop, tet_rule=tet_rule, **params)
-        return s.A.cpu().numpy(), s.b.cpu().numpy(), ref
+        return s.A.cpu().numpy(), s.b.cpu().numpy(), _reference(oracle, name, mesh)
     finally:
         s.close()
 
 
 @pytest.mark.parametrize("scatter", list(SCATTERS))
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_assembly_matches_oracle(oracle, name, precision, scatter):
     fea = engine()
     A, b, ref = _run_case(fea, oracle, name, precision, SCATTERS[scatter])
@@ -103,7 +113,7 @@ def test_inverted_element_is_reported_by_check():
     mesh.conn = conn.reshape(-1)
     s = fea.System.from_mesh(mesh, 3)
     try:
-        for precision in (0, 1):
+        for precision in (0, 1, 2):
             s.assemble(fea.make_operator(kind=1, precision=precision))
             with pytest.raises(fea.FeaError) as ei:
                 s.check()
