@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define FEA_ABI_VERSION 1
+#define FEA_ABI_VERSION 2
 
 typedef enum {
   FEA_OK = 0,
@@ -62,7 +62,11 @@ typedef enum { FEA_TET4 = 0, FEA_PYR5 = 1, FEA_PRISM6 = 2, FEA_HEX8 = 3 } fea_el
 
 typedef enum {
   FEA_OP_DIFFUSION = 0,  /* scalar, 1 dof/node: A_ab = int k(x) grad N_a . grad N_b, b_a = int f N_a */
-  FEA_OP_ELASTICITY = 1  /* 3 dofs/node, isotropic small strain: A = int B^T D B, b = int f N        */
+  FEA_OP_ELASTICITY = 1, /* 3 dofs/node, isotropic small strain: A = int B^T D B, b = int f N        */
+  FEA_OP_J2 = 2          /* 3 dofs/node, small-strain J2 plasticity with Voce hardening (the Gauss-point
+                            constitutive update of the solid element loop, Sec. 2.2 / 5.2): radial return
+                            from the committed state, A = int B^T D_ep B with the consistent tangent,
+                            b = f_int = int B^T sigma; see the J2 fields of fea_operator */
 } fea_op_kind;
 
 typedef enum {
@@ -94,6 +98,21 @@ typedef enum {
                              the block plan on the host (synchronous); later calls are stream-ordered. */
 } fea_scatter;
 
+/* Scheduling of the element loop (the GPU counterpart of the paper's dynamic
+ * load balancing, Sec. 4: the cost of an element is not known beforehand).
+ * A work item is a run of at most `chunk` consecutive elements of one type:
+ * for each type t in enum order, the elements of type t in upload order are
+ * cut into ceil(n_t / chunk) items (fea_work_items lists them). */
+typedef enum {
+  FEA_SCHED_PER_TYPE = 0, /* one launch per element type (per color class for FEA_SCATTER_COLOR) */
+  FEA_SCHED_STEAL = 1,    /* one persistent launch over every type: n_ctas CTAs take items in list
+                             order from a global counter (dynamic work stealing) */
+  FEA_SCHED_QUEUES = 2    /* one persistent launch: CTA c processes exactly the items
+                             queue_d[queue_off_d[c] .. queue_off_d[c+1]) in that order (static
+                             queues packed by the caller, e.g. longest-processing-time first on
+                             predicted costs); no stealing */
+} fea_schedule;
+
 /* Mesh description for fea_mesh_upload.  coords is xyz per node (AoS,
  * float64 [3*n_nodes]); element e has type types[e] and nodes
  * conn[conn_offsets[e] .. conn_offsets[e+1]) in the local order above.
@@ -123,6 +142,27 @@ typedef struct {
  *             call records on its stream -- events[0] before zeroing A and b,
  *             events[1] after zeroing, events[2 + j] after the j-th kernel it
  *             launches (only those with index < n_events are recorded).
+ *  schedule   fea_schedule (FEA_SCATTER_ATOMIC only for the persistent ones)
+ *  chunk      elements per work item (persistent schedules; 0 = 128)
+ *  n_ctas     persistent grid size (0 = 2 CTAs per SM); FEA_SCHED_QUEUES needs it
+ *  queue_d, queue_off_d  FEA_SCHED_QUEUES: int32 item ids and int64 [n_ctas + 1]
+ *             offsets (device); every item must appear exactly once (not checked)
+ *  item_ns_d  optional uint64 [n_items] (device): per item, the %globaltimer
+ *             nanoseconds its CTA spent on it (persistent schedules)
+ *  item_cta_d optional int32 [n_items] (device): the CTA that processed the item
+ *  J2 (kind FEA_OP_J2; young and poisson as for elasticity, tet4 always 4-point):
+ *   sigma_y(alpha) = sigma0 + hardening alpha + (sigma_inf - sigma0)(1 - exp(-delta alpha));
+ *   the Newton iteration on the consistency condition stops when |g| <= tol_g
+ *   sigma_y(alpha_n) or after an update of at most tol_step; more than max_iter
+ *   updates latches FEA_ERR_NO_CONVERGENCE.
+ *   u_d          float64 [n_nodes][3] nodal displacements (device)
+ *   state_in_d   float64 [n_elems][8][7] committed state per (element, point slot):
+ *                plastic strain (xx, yy, zz, xy, yz, xz tensor components), alpha;
+ *                NULL = virgin material.  Slots past the rule's point count are unused.
+ *   state_out_d  float64 [n_elems][8][7] updated state (may be NULL; not in place)
+ *   yield_out_d  uint8 [n_elems][8]: 1 where the point yielded (may be NULL)
+ *   iters_out_d  uint8 [n_elems][8]: Newton updates of the point (may be NULL)
+ *   Elements are indexed by original (upload) id.
  */
 typedef struct {
   int32_t kind;
@@ -135,6 +175,24 @@ typedef struct {
   void** events;
   int32_t n_events;
   int32_t reserved;
+  /* scheduling */
+  int32_t schedule;
+  int32_t chunk;
+  int32_t n_ctas;
+  int32_t reserved2;
+  const int32_t* queue_d;
+  const int64_t* queue_off_d;
+  uint64_t* item_ns_d;
+  int32_t* item_cta_d;
+  /* J2 */
+  double sigma0, sigma_inf, delta, hardening, tol_g, tol_step;
+  int32_t max_iter;
+  int32_t reserved3;
+  const double* u_d;
+  const double* state_in_d;
+  double* state_out_d;
+  uint8_t* yield_out_d;
+  uint8_t* iters_out_d;
 } fea_operator;
 
 typedef struct fea_mesh fea_mesh;
@@ -199,6 +257,20 @@ int fea_build_csr_pattern(fea_mesh* mesh, int ndof, int64_t* row_ptr_d, int32_t*
  * reported by fea_check (the values are then unspecified). */
 int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d,
                  const int32_t* node_map_d, double* A_vals_d, double* b_d, void* stream);
+
+/* Work items of the persistent schedules (fea_schedule): for each element
+ * type t in enum order, the elements of type t in upload order cut into runs
+ * of at most chunk elements (chunk 0 = 128).  Item i covers the elements of
+ * type type_h[i] with in-type ranks first_h[i] .. first_h[i] + count_h[i] - 1.
+ * *n_items receives the count; the three host arrays (each may be NULL) need
+ * *n_items entries.  Host call, no device work. */
+int fea_work_items(const fea_mesh* mesh, int chunk, int64_t* n_items, int32_t* type_h, int32_t* first_h,
+                   int32_t* count_h);
+
+/* Grid size of the persistent launch of op on mesh: op->n_ctas if positive,
+ * else the number of CTAs resident at once (occupancy x SM count), which is
+ * how many queues a FEA_SCHED_QUEUES packing should fill.  Host call. */
+int fea_persistent_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
 
 /* CSR row pointers from row lengths, allocating nothing on the device.
  * The paper has no counterpart: this is a service for callers that cannot let

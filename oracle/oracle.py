@@ -75,7 +75,12 @@ def lib():
 
 
 def _extra_signatures():
-    return {}
+    return {
+        "oracle_j2_point": (_i32, [_p, _p, _p, ctypes.c_double, _p, _p, _p, _p, _p, _p]),
+        "oracle_j2_element": (_i32, [_i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
+        "oracle_j2_assemble": (_i64, [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
+        "oracle_j2_sweep": (_i64, [_i64, _p, _p, _p, _p, _p, _p, ctypes.c_double, _p, _p]),
+    }
 
 
 def _ptr(a):
@@ -224,3 +229,99 @@ def err_metric(a, ref, S):
     err = float(np.max(np.abs(a[pos] - ref[pos]) / S[pos])) if pos.any() else 0.0
     zeros_ok = bool(np.all(a[~pos] == 0.0) and np.all(ref[~pos] == 0.0))
     return err, zeros_ok
+
+
+# ---------------------------------------------------------------------------
+# J2 plasticity with Voce hardening (j2_oracle.c)
+# ---------------------------------------------------------------------------
+
+class NoConvergence(RuntimeError):
+    pass
+
+
+J2_DEFAULTS = dict(young=1.0, poisson=0.3, sigma0=1e-3, sigma_inf=3e-3, delta=300.0, hardening=1e-2,
+                   tol_g=1e-13, tol_step=1e-15, max_iter=12)
+
+
+def j2_params(**kw) -> np.ndarray:
+    """Material and Newton parameters in the oracle's order (defaults: the C4 workload)."""
+    p = dict(J2_DEFAULTS, **kw)
+    return np.array([p["young"], p["poisson"], p["sigma0"], p["sigma_inf"], p["delta"], p["hardening"],
+                     p["tol_g"], p["tol_step"], p["max_iter"]], dtype=np.float64)
+
+
+def j2_point(eps, eps_p_n=None, alpha_n=0.0, **kw):
+    """Radial return at one point: eps, eps_p tensor components (xx, yy, zz, xy, yz, xz).
+
+    Returns dict(sigma [6], D [6, 6] on engineering strain, eps_p [6], alpha,
+    iters, yielded).
+    """
+    prm = j2_params(**kw)
+    eps = _c(eps, np.float64)
+    epn = _c(np.zeros(6) if eps_p_n is None else eps_p_n, np.float64)
+    sig = np.zeros(6); D = np.zeros(36); ep = np.zeros(6)
+    al = ctypes.c_double(); it = ctypes.c_int(); yl = ctypes.c_int()
+    rc = lib().oracle_j2_point(_ptr(prm), _ptr(eps), _ptr(epn), float(alpha_n), _ptr(sig), _ptr(D), _ptr(ep),
+                               ctypes.byref(al), ctypes.byref(it), ctypes.byref(yl))
+    if rc:
+        raise NoConvergence("return map did not converge")
+    return dict(sigma=sig, D=D.reshape(6, 6), eps_p=ep, alpha=al.value, iters=it.value, yielded=yl.value)
+
+
+def j2_element(etype, X, U, state_n=None, **kw):
+    """Tangent, internal force and normwise scales of one element (4-point tet rule)."""
+    prm = j2_params(**kw)
+    X = _c(X, np.float64); U = _c(U, np.float64)
+    n = 3 * NODES[etype]
+    Ae = np.zeros((n, n)); be = np.zeros(n); Ne = np.zeros((n, n)); Nb = np.zeros(n)
+    st = np.zeros((8, 7)); it = np.zeros(8, dtype=np.int32); yl = np.zeros(8, dtype=np.int32)
+    sn = None if state_n is None else _c(state_n, np.float64)
+    rc = lib().oracle_j2_element(etype, _ptr(prm), _ptr(X), _ptr(U), _ptr(sn), _ptr(Ae), _ptr(be), _ptr(Ne),
+                                 _ptr(Nb), _ptr(st), _ptr(it), _ptr(yl))
+    if rc == 1:
+        raise InvertedElement(-1)
+    if rc == 2:
+        raise NoConvergence("return map did not converge")
+    return dict(A=Ae, b=be, NA=Ne, Nb=Nb, state=st, iters=it, yielded=yl)
+
+
+def j2_assemble(mesh, U, state_n=None, pat=None, **kw):
+    """Tangent matrix and internal force of the whole mesh (3 dofs per node), element-index order.
+
+    U: [n_nodes, 3] displacements; state_n: [E, 8, 7] (None = virgin).
+    Returns dict(row_ptr, col_idx, node_map, A, b, NA, Nb, state [E, 8, 7],
+    iters [E, 8], yielded [E, 8]).
+    """
+    if pat is None:
+        pat = pattern(mesh, 3)
+    rps, cols, nmap = pat
+    prm = j2_params(**kw)
+    E = mesh.n_elems
+    A = np.zeros(cols.shape[0]); NA = np.zeros_like(A)
+    b = np.zeros(mesh.n_nodes * 3); Nb = np.zeros_like(b)
+    st = np.zeros((E, 8, 7)); it = np.zeros((E, 8), dtype=np.int32); yl = np.zeros((E, 8), dtype=np.uint8)
+    sn = None if state_n is None else _c(state_n, np.float64)
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64); U = _c(U, np.float64)
+    rc = lib().oracle_j2_assemble(mesh.n_nodes, E, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords), _ptr(prm),
+                                  _ptr(U), _ptr(sn), _ptr(rps), _ptr(nmap), _ptr(A), _ptr(b), _ptr(NA), _ptr(Nb),
+                                  _ptr(st), _ptr(it), _ptr(yl))
+    if rc < 0 and -rc <= E:
+        raise InvertedElement(-rc - 1)
+    if rc < 0:
+        raise NoConvergence(f"return map of element {-rc - E - 1} did not converge")
+    return dict(row_ptr=rps, col_idx=cols, node_map=nmap, A=A, b=b, NA=NA, Nb=Nb, state=st, iters=it, yielded=yl)
+
+
+def j2_sweep(mesh, U, scale=1.0, state_n=None, want_state=False, **kw):
+    """Count the yielding Gauss points at displacement scale*U (no assembly); optionally the new state."""
+    prm = j2_params(**kw)
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64); U = _c(U, np.float64)
+    st = np.zeros((mesh.n_elems, 8, 7)) if want_state else None
+    sn = None if state_n is None else _c(state_n, np.float64)
+    n = lib().oracle_j2_sweep(mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords), _ptr(prm), _ptr(U),
+                              float(scale), _ptr(sn), _ptr(st))
+    if n < 0:
+        raise NoConvergence("inverted element or failed return map")
+    return (int(n), st) if want_state else int(n)

@@ -22,6 +22,7 @@
 
 #include "element.cuh"
 #include "fea_internal.cuh"
+#include "sched.cuh"
 
 namespace fea {
 
@@ -350,13 +351,13 @@ struct TileCfg {
 // phases 0 and 1 for the tile of elements [e0, e0 + EPC)
 template <class Cfg, int OP, int PREC>
 __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefRule& rr, const AsmParams& P,
-                                              int64_t e0) {
+                                              int64_t e0, int64_t n_end) {
   constexpr int NN = Cfg::NN, NQ = Cfg::NQ, EPC = Cfg::EPC;
   constexpr bool kModal = Cfg::kModal;
   for (int t = threadIdx.x; t < EPC * NN; t += Cfg::THREADS) {
     const int le = t / NN, a = t % NN;
     const int64_t et = e0 + le;
-    if (et < P.n) {
+    if (et < n_end) {
       const int64_t node = P.tconn[group_index(P, et) * NN + a];
       sm.X[le][a][0] = P.coords[3 * node + 0];
       sm.X[le][a][1] = P.coords[3 * node + 1];
@@ -374,7 +375,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
       if (t < EPC * 8) {
         const int le = t >> 3, p = t & 7;
         const int64_t et = e0 + le;
-        const bool valid = et < P.n;
+        const bool valid = et < n_end;
         const int a = hex8_corner_node(p);
         double v[3];
 #pragma unroll
@@ -408,7 +409,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
   for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
     const int le = t / NQ, q = t % NQ;
     const int64_t et = e0 + le;
-    if (et >= P.n) continue;
+    if (et >= n_end) continue;
     if (all64) {
       geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
     } else {
@@ -420,7 +421,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
     for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
       const int le = t / NQ, q = t % NQ;
       const int64_t et = e0 + le;
-      if (et < P.n && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
+      if (et < n_end && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
     }
   }
   __syncthreads();
@@ -484,64 +485,207 @@ __device__ __forceinline__ void row_block(const typename Cfg::Smem& sm, const Re
   }
 }
 
-// FP64 value of a contribution: exact integer widening of FP32 (keeps the
-// FP64 pipe free), identity for FP64
-__device__ __forceinline__ double widen(float x) { return f32_to_f64_exact(x); }
-__device__ __forceinline__ double widen(double x) { return x; }
-
-// add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain
-// read-modify-write when no other element of the launch touches the entry
-// (COLOR: the launch holds one color class, Alg. "coloring")
-template <int SC>
-__device__ __forceinline__ void scatter_add(double* p, double v) {
-  if constexpr (SC == FEA_SCATTER_ATOMIC)
-    atomicAdd(p, v);
-  else
-    *p += v;
-}
-
-// Tile kernel: integrate EPC elements, scatter each row block (a, b0..b0+NB)
+// One tile of EPC elements starting at launch index e0 (elements at or past
+// n_end are skipped): integrate, then scatter each row block (a, b0..b0+NB).
+// Every thread of the CTA must call it; it ends with the shared memory free.
 template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
-__global__ void __launch_bounds__(128) k_assemble_tile(const __grid_constant__ RefRule rr,
-                                                       const __grid_constant__ AsmParams P) {
+__device__ __forceinline__ void tile_body(typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem& sm,
+                                          const RefRule& rr, const AsmParams& P, int64_t e0, int64_t n_end) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   using R = typename Cfg::R;
   constexpr int NN = Cfg::NN, D = Cfg::D, NB = Cfg::NB, LPE = Cfg::LPE, EPW = Cfg::EPW;
-  __shared__ typename Cfg::Smem sm;
-  const int64_t e0 = (int64_t)blockIdx.x * Cfg::EPC;
-  tile_geometry<Cfg, OP, PREC>(sm, rr, P, e0);
+  tile_geometry<Cfg, OP, PREC>(sm, rr, P, e0, n_end);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lw = lane / LPE;
-  if (lw >= EPW) return;
   const int le = warp * EPW + lw;
   const int64_t et = e0 + le;
-  if (et >= P.n) return;
-  const int r = lane % LPE;
-  const int a = r % NN, b0 = (r / NN) * NB;
+  if (lw < EPW && et < n_end) {
+    const int r = lane % LPE;
+    const int a = r % NN, b0 = (r / NN) * NB;
 
-  R K[NB][D][D], rhs[D];
-  row_block<Cfg, OP>(sm, rr, P, le, a, b0, K, rhs);
+    R K[NB][D][D], rhs[D];
+    row_block<Cfg, OP>(sm, rr, P, le, a, b0, K, rhs);
 
-  const int64_t g = group_index(P, et);
-  const int64_t node = P.tconn[g * NN + a];
-  const int64_t id = P.ids ? (int64_t)P.ids[g] : g;
-  const int64_t moff = P.mapoff ? P.mapoff[g] : id * NN * NN;
-  const int32_t* mp = P.node_map + moff + a * NN + b0;
-  int64_t rb[D];
+    const int64_t g = group_index(P, et);
+    const int64_t node = P.tconn[g * NN + a];
+    const int64_t id = P.ids ? (int64_t)P.ids[g] : g;
+    const int64_t moff = P.mapoff ? P.mapoff[g] : id * NN * NN;
+    const int32_t* mp = P.node_map + moff + a * NN + b0;
+    int64_t rb[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) rb[c] = P.row_ptr[D * node + c];
+    for (int c = 0; c < D; ++c) rb[c] = P.row_ptr[D * node + c];
 #pragma unroll
-  for (int bb = 0; bb < NB; ++bb) {
-    const int64_t k = mp[bb];
+    for (int bb = 0; bb < NB; ++bb) {
+      const int64_t k = mp[bb];
 #pragma unroll
-    for (int c = 0; c < D; ++c)
+      for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int cc = 0; cc < D; ++cc) scatter_add<SC>(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
+        for (int cc = 0; cc < D; ++cc) scatter_add<SC>(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
+    }
+    if (b0 == 0)
+#pragma unroll
+      for (int c = 0; c < D; ++c) scatter_add<SC>(P.b + D * node + c, widen(rhs[c]));
   }
-  if (b0 == 0)
-#pragma unroll
-    for (int c = 0; c < D; ++c) scatter_add<SC>(P.b + D * node + c, widen(rhs[c]));
+  __syncthreads();
+}
+
+// Tile kernel: one tile per CTA
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
+__global__ void __launch_bounds__(128) k_assemble_tile(const __grid_constant__ RefRule rr,
+                                                       const __grid_constant__ AsmParams P) {
+  __shared__ typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem sm;
+  tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC>(sm, rr, P, (int64_t)blockIdx.x * TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::EPC,
+                                             P.n);
+}
+
+// ---------------------------------------------------------------------------
+// persistent schedule: one launch over every element type (sched.cuh)
+// ---------------------------------------------------------------------------
+__constant__ RefRule c_rules[kNumRules];
+
+struct PersistAsmArgs {
+  AsmParams table[kNumTypes];  // entry t: the group of element type t
+  int32_t slot[kNumTypes];     // its quadrature rule
+  SchedArgs S;
+};
+
+template <int OP, int PREC>
+struct PersistCfg {
+  static constexpr int S2 = (OP == FEA_OP_ELASTICITY && PREC == FEA_FP64) ? 2 : 1;
+  template <int TYPE, int SLOT, int SPLIT>
+  static constexpr size_t bytes() { return sizeof(typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem); }
+  static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t smem =
+      mx(mx(mx(bytes<FEA_TET4, kRuleTet1, 1>(), bytes<FEA_TET4, kRuleTet4, 1>()), bytes<FEA_PYR5, kRulePyr8, 1>()),
+         mx(bytes<FEA_PRISM6, kRulePrism6, S2>(), bytes<FEA_HEX8, kRuleHex8, S2>()));
+};
+
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+__device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams& P, int64_t first, int64_t end) {
+  using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
+  auto& sm = *reinterpret_cast<typename Cfg::Smem*>(raw);
+  for (int64_t e0 = first; e0 < end; e0 += Cfg::EPC)
+    tile_body<TYPE, SLOT, OP, PREC, SPLIT, FEA_SCATTER_ATOMIC>(sm, c_rules[SLOT], P, e0, end);
+}
+
+template <int OP, int PREC>
+__global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ PersistAsmArgs A) {
+  constexpr int S2 = PersistCfg<OP, PREC>::S2;
+  extern __shared__ __align__(16) unsigned char persist_smem[];
+  __shared__ int s_item;
+  int k = 0;
+  for (;;) {
+    const int item = sched_next(A.S, k, &s_item);
+    if (item < 0) break;
+    const uint64_t t0 = global_ns();
+    const WorkItem it = A.S.items[item];
+    const AsmParams& P = A.table[it.entry];
+    const int64_t first = it.first, end = (int64_t)it.first + it.count;
+    switch (A.slot[it.entry]) {
+      case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
+      case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
+      case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
+      case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
+      default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
+    }
+    sched_record(A.S, item, t0);
+  }
+}
+
+int init_rule_constants() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  FEA_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 64 && done[dev]) return FEA_OK;
+  RefRule all[kNumRules];
+  for (int r = 0; r < kNumRules; ++r) all[r] = host_rule(r);
+  FEA_CUDA(cudaMemcpyToSymbol(c_rules, all, sizeof(all)));
+  if (dev < 64) done[dev] = true;
+  return init_rule_constants_j2();
+}
+
+static AsmParams base_params(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                             double* A, double* b) {
+  AsmParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.coords = m->coords;
+  P.row_ptr = row_ptr;
+  P.node_map = node_map;
+  P.A = A;
+  P.b = b;
+  P.st = m->status;
+  P.k0 = op->k0;
+  P.k2 = op->k2;
+  P.src = op->source;
+  const double E = op->young, nu = op->poisson;
+  P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  P.mu = E / (2.0 * (1.0 + nu));
+  for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
+  P.geo64 = op->precision != FEA_FP32_ADAPTIVE;
+  return P;
+}
+
+static int rule_slot_of(int type, int tet_rule) {
+  switch (type) {
+    case FEA_TET4: return tet_rule ? kRuleTet4 : kRuleTet1;
+    case FEA_PYR5: return kRulePyr8;
+    case FEA_PRISM6: return kRulePrism6;
+    default: return kRuleHex8;
+  }
+}
+
+template <int OP, int PREC>
+static int launch_persistent_t(const PersistAsmArgs& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
+  constexpr size_t smem = PersistCfg<OP, PREC>::smem;
+  auto kern = k_persistent<OP, PREC>;
+  if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = n_ctas;
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    FEA_CUDA(cudaGetDevice(&dev));
+    FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FEA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid_out) *grid_out = grid;
+  if (!dry) {
+    kern<<<grid, 128, smem, s>>>(args);
+    FEA_CUDA(cudaGetLastError());
+  }
+  return FEA_OK;
+}
+
+// Persistent launch of the diffusion / elasticity tile over every type group.
+// n_ctas <= 0 selects the resident-CTA count (occupancy x SMs); the grid used
+// is returned in *grid_out.  dry = true only computes the grid.
+int launch_persistent_assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                               double* A, double* b, const SchedArgs& S, int n_ctas, bool dry, cudaStream_t s,
+                               int* grid_out) {
+  PersistAsmArgs args;
+  std::memset(&args, 0, sizeof(args));
+  const AsmParams base = base_params(op, m, row_ptr, node_map, A, b);
+  for (int t = 0; t < kNumTypes; ++t) {
+    args.table[t] = base;
+    const TypeGroup& g = m->group[t];
+    args.table[t].tconn = g.conn;
+    args.table[t].ids = g.ids;
+    args.table[t].mapoff = g.mapoff;
+    args.table[t].n = g.n;
+    args.slot[t] = rule_slot_of(t, op->tet_rule);
+  }
+  args.S = S;
+  int rc;
+  const bool f64 = op->precision == FEA_FP64;
+  if (op->kind == FEA_OP_DIFFUSION)
+    rc = f64 ? launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP64>(args, n_ctas, dry, s, grid_out)
+             : launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+  else
+    rc = f64 ? launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP64>(args, n_ctas, dry, s, grid_out)
+             : launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -582,16 +726,20 @@ static int launch_group(int type, int tet_rule, const AsmParams& P, cudaStream_t
 int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
              double* b, cudaStream_t s) {
   if (!op || !m || !row_ptr || !node_map || !A || !b) return fail(FEA_ERR_ARG, "fea_assemble: null argument");
-  if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY)
+  if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY && op->kind != FEA_OP_J2)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
   if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE && op->precision != FEA_FP32_ADAPTIVE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
   if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_ROWS)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown scatter variant");
   if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
+  if (op->schedule < FEA_SCHED_PER_TYPE || op->schedule > FEA_SCHED_QUEUES)
+    return fail(FEA_ERR_ARG, "fea_assemble: unknown schedule");
   const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
   if (m->pattern_ndof != D || !m->pattern_built)
     return fail(FEA_ERR_ARG, "fea_assemble: build the pattern and map for ndof = " + std::to_string(D) + " first");
+  if (op->schedule != FEA_SCHED_PER_TYPE) return assemble_persistent(op, m, row_ptr, node_map, A, b, s);
+  if (op->kind == FEA_OP_J2) return assemble_j2(op, m, row_ptr, node_map, A, b, s);
   if (op->kind == FEA_OP_ELASTICITY) {
     if (!(op->poisson > -1.0 && op->poisson < 0.5)) return fail(FEA_ERR_ARG, "fea_assemble: poisson must be in (-1, 0.5)");
   }
@@ -710,6 +858,10 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
 
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
   if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
+  if (op->schedule != FEA_SCHED_PER_TYPE) {
+    *n = 1;  // one persistent launch over every type
+    return FEA_OK;
+  }
   if (op->scatter == FEA_SCATTER_ROWS || op->scatter == FEA_SCATTER_BLOCK) {
     *n = geometry_launches(m) + 1;  // geometry pass per element type, then the task kernel
     return FEA_OK;

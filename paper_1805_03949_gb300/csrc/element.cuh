@@ -173,4 +173,20 @@ __device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {
 }
 
 
+// FP64 value of a contribution: exact integer widening of FP32 (keeps the
+// FP64 pipe free), identity for FP64
+__device__ __forceinline__ double widen(float x) { return f32_to_f64_exact(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+
+// add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain
+// read-modify-write when no other element of the launch touches the entry
+// (COLOR: the launch holds one color class, Alg. "coloring")
+template <int SC>
+__device__ __forceinline__ void scatter_add(double* p, double v) {
+  if constexpr (SC == FEA_SCATTER_ATOMIC)
+    atomicAdd(p, v);
+  else
+    *p += v;
+}
+
 }  // namespace fea

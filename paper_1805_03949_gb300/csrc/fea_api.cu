@@ -55,6 +55,7 @@ static void free_mesh(fea_mesh* m) {
   drop_rows_plans(m);
   cudaFree(m->geo[0]);
   cudaFree(m->geo[1]);
+  fea::free_sched(m);
   free_color_plan(m);
   if (m->blocks) {
     free_rows_plan(m->blocks);
@@ -183,6 +184,13 @@ static int upload_mesh(const fea_mesh_desc* d, cudaStream_t s, fea_mesh** out) {
   if (e != cudaSuccess) {
     free_mesh(m);
     return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  {
+    const int rc = init_rule_constants();  // synchronous copy, so never inside a stream capture
+    if (rc) {
+      free_mesh(m);
+      return rc;
+    }
   }
   *out = m;
   return FEA_OK;

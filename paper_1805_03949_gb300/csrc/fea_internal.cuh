@@ -11,6 +11,7 @@
 #include "fea_gb300.h"
 #include "geometry.cuh"
 #include "rows.cuh"
+#include "sched.cuh"
 
 namespace fea {
 
@@ -80,6 +81,11 @@ struct fea_mesh {
   fea::RowsPlan* blocks = nullptr;              // FEA_SCATTER_BLOCK plan (blocks.cu)
   int block_elems = 64;                         // elements per block of FEA_SCATTER_BLOCK
   int rows_block_nodes = 64;
+  // persistent schedules (persistent.cu): work items of the last chunk size
+  int items_chunk = 0;
+  std::vector<fea::WorkItem> items_h;
+  fea::WorkItem* items = nullptr;               // device copy of items_h
+  int32_t* sched_counter = nullptr;             // FEA_SCHED_STEAL counter
 };
 
 namespace fea {
@@ -110,6 +116,21 @@ int exclusive_scan_i32(const int32_t* in, int64_t n, int64_t* out, cudaStream_t 
 int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
              double* A, double* b, cudaStream_t s);
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n);
+
+// persistent schedules: launchers (assemble.cu, j2.cu) and host side (persistent.cu)
+int launch_persistent_assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                               double* A, double* b, const SchedArgs& S, int n_ctas, bool dry, cudaStream_t s,
+                               int* grid_out);
+int launch_persistent_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                         double* A, double* b, const SchedArgs& S, int n_ctas, bool dry, cudaStream_t s,
+                         int* grid_out);
+int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                        double* A, double* b, cudaStream_t s);
+int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
+                double* b, cudaStream_t s);
+int init_rule_constants();     // __constant__ quadrature tables of the persistent kernels (current device)
+int init_rule_constants_j2();
+void free_sched(fea_mesh* m);
 
 // color.cu
 int build_color_plan(fea_mesh* m, cudaStream_t s);

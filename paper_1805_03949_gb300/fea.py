@@ -29,7 +29,8 @@ FEA_ERR_INDEX_OVERFLOW = -7
 FEA_ERR_UNSUPPORTED = -8
 
 FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
-FEA_OP_DIFFUSION, FEA_OP_ELASTICITY = 0, 1
+FEA_OP_DIFFUSION, FEA_OP_ELASTICITY, FEA_OP_J2 = 0, 1, 2
+FEA_SCHED_PER_TYPE, FEA_SCHED_STEAL, FEA_SCHED_QUEUES = 0, 1, 2
 FEA_FP64, FEA_FP32_INTEGRATE, FEA_FP32_ADAPTIVE = 0, 1, 2
 FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS = 0, 1, 2, 3
 
@@ -52,7 +53,15 @@ class fea_operator(ctypes.Structure):
                 ("tet_rule", ctypes.c_int32), ("k0", ctypes.c_double), ("k2", ctypes.c_double),
                 ("source", ctypes.c_double), ("young", ctypes.c_double), ("poisson", ctypes.c_double),
                 ("body_force", ctypes.c_double * 3), ("events", ctypes.POINTER(ctypes.c_void_p)),
-                ("n_events", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_events", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("chunk", ctypes.c_int32), ("n_ctas", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32), ("queue_d", ctypes.c_void_p), ("queue_off_d", ctypes.c_void_p),
+                ("item_ns_d", ctypes.c_void_p), ("item_cta_d", ctypes.c_void_p),
+                ("sigma0", ctypes.c_double), ("sigma_inf", ctypes.c_double), ("delta", ctypes.c_double),
+                ("hardening", ctypes.c_double), ("tol_g", ctypes.c_double), ("tol_step", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("reserved3", ctypes.c_int32),
+                ("u_d", ctypes.c_void_p), ("state_in_d", ctypes.c_void_p), ("state_out_d", ctypes.c_void_p),
+                ("yield_out_d", ctypes.c_void_p), ("iters_out_d", ctypes.c_void_p)]
 
 
 def _load():
@@ -73,6 +82,8 @@ def _load():
         "fea_check": (I32, [P, P]),
         "fea_assemble_launches": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_row_ptr_from_counts_noalloc": (I32, [P, I64, P, P]),
+        "fea_work_items": (I32, [P, I32, ctypes.POINTER(I64), P, P, P]),
+        "fea_persistent_grid": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_mesh_set_rows_block": (I32, [P, I32]),
         "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
         "fea_color_info": (I32, [P, P, ctypes.POINTER(I32)]),
@@ -217,6 +228,23 @@ def fea_color_info(h, n_elems: int):
     return n.value, colors
 
 
+def fea_work_items(h, chunk: int = 0):
+    """Work items of the persistent schedules: (type, first, count) int32 arrays."""
+    import numpy as np
+    n = ctypes.c_int64()
+    _check(_lib.fea_work_items(h, chunk, ctypes.byref(n), None, None, None))
+    t = np.zeros(n.value, dtype=np.int32); f = np.zeros_like(t); c = np.zeros_like(t)
+    _check(_lib.fea_work_items(h, chunk, ctypes.byref(n), t.ctypes.data_as(ctypes.c_void_p),
+                               f.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p)))
+    return t, f, c
+
+
+def fea_persistent_grid(op: "fea_operator", h) -> int:
+    n = ctypes.c_int32()
+    _check(_lib.fea_persistent_grid(ctypes.byref(op), h, ctypes.byref(n)))
+    return int(n.value)
+
+
 def fea_assemble_launches(op: "fea_operator", h) -> int:
     n = ctypes.c_int()
     _check(_lib.fea_assemble_launches(ctypes.byref(op), h, ctypes.byref(n)))
@@ -239,14 +267,30 @@ def set_events(op: "fea_operator", events) -> None:
 # convenience: operator construction and a mesh + pattern + buffers bundle
 # ---------------------------------------------------------------------------
 
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
 def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER_ATOMIC, tet_rule=1,
-                  k0=1.0, k2=0.0, source=1.0, young=1.0, poisson=0.3, body_force=(1.0, 1.0, 1.0)) -> fea_operator:
+                  k0=1.0, k2=0.0, source=1.0, young=1.0, poisson=0.3, body_force=(1.0, 1.0, 1.0),
+                  schedule=FEA_SCHED_PER_TYPE, chunk=0, n_ctas=0, queue=None, queue_off=None, item_ns=None,
+                  item_cta=None, sigma0=1e-3, sigma_inf=3e-3, delta=300.0, hardening=1e-2, tol_g=1e-13,
+                  tol_step=1e-15, max_iter=12, u=None, state_in=None, state_out=None, yield_out=None,
+                  iters_out=None) -> fea_operator:
+    """Operator struct; tensors (device) are referenced by pointer, the caller keeps them alive."""
     op = fea_operator()
     op.kind, op.precision, op.scatter, op.tet_rule = kind, precision, scatter, tet_rule
     op.k0, op.k2, op.source = k0, k2, source
     op.young, op.poisson = young, poisson
     for c in range(3):
         op.body_force[c] = body_force[c]
+    op.schedule, op.chunk, op.n_ctas = schedule, chunk, n_ctas
+    op.queue_d, op.queue_off_d = _dptr(queue), _dptr(queue_off)
+    op.item_ns_d, op.item_cta_d = _dptr(item_ns), _dptr(item_cta)
+    op.sigma0, op.sigma_inf, op.delta, op.hardening = sigma0, sigma_inf, delta, hardening
+    op.tol_g, op.tol_step, op.max_iter = tol_g, tol_step, max_iter
+    op.u_d, op.state_in_d, op.state_out_d = _dptr(u), _dptr(state_in), _dptr(state_out)
+    op.yield_out_d, op.iters_out_d = _dptr(yield_out), _dptr(iters_out)
     return op
 
 

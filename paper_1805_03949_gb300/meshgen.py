@@ -340,3 +340,14 @@ def fourier_displacement(coords: np.ndarray, amplitude: float, seed: int = 4,
     for m in range(modes):
         u += np.sin(2 * np.pi * coords @ k[m] + phi[m])[:, None] * a[m][None, :]
     return amplitude * u
+
+
+def j2_workload(n: int = 96, amplitude: float = 1.0, seed_mesh: int = 6, seed_u: int = 4):
+    """Elastoplastic hex8 workload: n^3 jittered cube (+-0.2h, PCG64(seed_mesh)) and the
+    nodal displacement field fourier_displacement(coords, amplitude, seed_u).
+
+    The load is applied in two steps, 0.5 u then u; the amplitude that makes
+    about 30% of the Gauss points yield in the second step is a stored fixture.
+    """
+    mesh = hex_cube(n, 0.2, seed_mesh)
+    return mesh, fourier_displacement(mesh.coords, amplitude, seed=seed_u)

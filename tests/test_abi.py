@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(clib):
 
 def test_host_side_argument_checks(clib):
     clib.fea_abi_version.restype = ctypes.c_int
-    assert clib.fea_abi_version() == 1
+    assert clib.fea_abi_version() == 2
     clib.fea_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
     rc = clib.fea_mesh_upload(None, None, ctypes.byref(out))
@@ -52,3 +52,30 @@ def test_host_side_argument_checks(clib):
     assert clib.fea_mesh_info(None, ctypes.byref(n), None, None) == -1
     assert clib.fea_assemble(None, None, None, None, None, None, None) == -1
     assert clib.fea_check(None, None) == -1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof and field offsets of the ctypes structs equal the C compiler's view of the header."""
+    from paper_1805_03949_gb300 import fea
+    probe = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fea_gb300.h"', 'int main(void) {']
+    for cname, cls in (("fea_operator", fea.fea_operator), ("fea_mesh_desc", fea.fea_mesh_desc)):
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines.append("return 0; }")
+    probe.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        cname, field, value = line.split()
+        cls = fea.fea_operator if cname == "fea_operator" else fea.fea_mesh_desc
+        expect = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert int(value) == expect, (cname, field, value, expect)
+        seen += 1
+    assert seen == len(fea.fea_operator._fields_) + len(fea.fea_mesh_desc._fields_) + 2
