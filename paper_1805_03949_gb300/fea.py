@@ -83,6 +83,15 @@ def _load():
         "fea_assemble_launches": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_row_ptr_from_counts_noalloc": (I32, [P, I64, P, P]),
         "fea_work_items": (I32, [P, I32, ctypes.POINTER(I64), P, P, P]),
+        "fea_costmodel_create": (I32, [I32, P, ctypes.POINTER(P)]),
+        "fea_costmodel_destroy": (I32, [P]),
+        "fea_costmodel_get_params": (I32, [P, P, P]),
+        "fea_costmodel_fit_scaler": (I32, [P, P, P, I64, P]),
+        "fea_costmodel_grad": (I32, [P, P, P, I64, P, P, P]),
+        "fea_costmodel_train": (I32, [P, P, P, I64, I32, ctypes.c_float, P, P]),
+        "fea_costmodel_predict": (I32, [P, P, I64, P, P]),
+        "fea_item_features": (I32, [P, I32, P, P, P, P]),
+        "fea_pack_lpt": (I32, [P, I64, I32, P, P, P]),
         "fea_persistent_grid": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_mesh_set_rows_block": (I32, [P, I32]),
         "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
@@ -245,6 +254,74 @@ def fea_persistent_grid(op: "fea_operator", h) -> int:
     return int(n.value)
 
 
+# ---------------------------------------------------------------------------
+# learned cost model and queue packing (costmodel.cu)
+# ---------------------------------------------------------------------------
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def fea_costmodel_create(n_in: int, params) -> ctypes.c_void_p:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(_lib.fea_costmodel_create(n_in, _np_ptr(p), ctypes.byref(h)))
+    return h
+
+
+def fea_costmodel_destroy(h):
+    _check(_lib.fea_costmodel_destroy(h))
+
+
+def fea_costmodel_get_params(h, n_in: int):
+    import numpy as np
+    n = 32 * n_in + 32 + 32 * 32 + 32 + 32 + 1
+    p = np.zeros(n, dtype=np.float32); sc = np.zeros(2 * n_in + 2, dtype=np.float32)
+    _check(_lib.fea_costmodel_get_params(h, _np_ptr(p), _np_ptr(sc)))
+    return p, sc
+
+
+def fea_costmodel_fit_scaler(h, X, y, stream=None):
+    _check(_lib.fea_costmodel_fit_scaler(h, _dptr(X), _dptr(y), X.shape[0], _stream(stream)))
+
+
+def fea_costmodel_grad(h, X, y, n_params: int, stream=None):
+    g = torch.empty(n_params, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(_lib.fea_costmodel_grad(h, _dptr(X), _dptr(y), X.shape[0], _dptr(g), _dptr(loss), _stream(stream)))
+    return g, loss
+
+
+def fea_costmodel_train(h, X, y, epochs: int, lr: float, stream=None):
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(_lib.fea_costmodel_train(h, _dptr(X), _dptr(y), X.shape[0], epochs, lr, _dptr(loss), _stream(stream)))
+    return loss
+
+
+def fea_costmodel_predict(h, X, stream=None):
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(_lib.fea_costmodel_predict(h, _dptr(X), X.shape[0], _dptr(y), _stream(stream)))
+    return y
+
+
+def fea_item_features(h, chunk: int, n_items: int, u=None, state_in=None, device="cuda", stream=None):
+    X = torch.empty((n_items, 6), dtype=torch.float32, device=device)
+    _check(_lib.fea_item_features(h, chunk, _dptr(u),
+                                  _dptr(state_in), _dptr(X), _stream(stream)))
+    return X
+
+
+def fea_pack_lpt(costs, n_queues: int):
+    """Host LPT packing: (queue ids int32, offsets int64 [n_queues + 1], loads float64)."""
+    import numpy as np
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    q = np.zeros(len(c), dtype=np.int32); off = np.zeros(n_queues + 1, dtype=np.int64)
+    load = np.zeros(n_queues, dtype=np.float64)
+    _check(_lib.fea_pack_lpt(_np_ptr(c), len(c), n_queues, _np_ptr(q), _np_ptr(off), _np_ptr(load)))
+    return q, off, load
+
+
 def fea_assemble_launches(op: "fea_operator", h) -> int:
     n = ctypes.c_int()
     _check(_lib.fea_assemble_launches(ctypes.byref(op), h, ctypes.byref(n)))
@@ -266,10 +343,6 @@ def set_events(op: "fea_operator", events) -> None:
 # ---------------------------------------------------------------------------
 # convenience: operator construction and a mesh + pattern + buffers bundle
 # ---------------------------------------------------------------------------
-
-def _dptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
-
 
 def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER_ATOMIC, tet_rule=1,
                   k0=1.0, k2=0.0, source=1.0, young=1.0, poisson=0.3, body_force=(1.0, 1.0, 1.0),
