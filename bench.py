@@ -325,8 +325,8 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None,
             "dtype": "f32 integrate + f64 accumulate" if "fp32" in head else "f64",
             "data": "synthetic (seeded jittered hex8 cube; the paper's meshes are not available)",
-            "config": {"workload": "hex8 linear elasticity, 128^3 jittered cube (+-0.2h, PCG64 seed 2), "
-                                   "2,097,152 elements, 513,599,625 nonzeros, 2x2x2 Gauss",
+            "config": {"workload": f"hex8 linear elasticity, {args.n}^3 jittered cube (+-0.2h, PCG64 seed 2), "
+                                   f"{E:,} elements, {nnz:,} nonzeros, 2x2x2 Gauss",
                        "variant": head, "l2": "inputs larger than L2 (A alone is 4.1 GB)",
                        "parallelism": f"replicas x{world} (partial-row, no exchange)"},
             "roofline": roof,
@@ -350,11 +350,162 @@ def run_ours(args, rank, world, local_rank):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
+        if world == 1 and args.configs:
+            sysm.close()
+            torch.cuda.empty_cache()
+            line["configs"] = other_configs(args, dev)
         print(json.dumps(line), flush=True)
     sysm.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the other workloads (one GPU, after the headline line's measurement)
+# ---------------------------------------------------------------------------
+
+def _time_calls(fn, steps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(statistics.median(ts))
+
+
+def config_hybrid(dev, steps=5):
+    """Hybrid tet/pyramid/prism/hex diffusion, k = 1 + x^2, degree-2 rules: per-type launches
+    against one persistent launch over every type (work stealing)."""
+    from paper_1805_03949_gb300 import fea, meshgen as mg
+    mesh = mg.hybrid_cube(100, 3)
+    s = fea.System.from_mesh(mesh, 1, device=dev, with_cols=False)
+    try:
+        kw = dict(kind=0, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
+        ops = {"fp64_per_type": fea.make_operator(precision=0, **kw),
+               "fp32_per_type": fea.make_operator(precision=1, **kw),
+               "fp32_persistent_steal": fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, **kw)}
+        out = {}
+        for name, op in ops.items():
+            ms = _time_calls(lambda: s.assemble(op), steps)
+            s.check()
+            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        return {"workload": "hybrid 100^3 cube, 4,528,302 elements (tet 40 / pyr 10 / prism 20 / hex 30 %), "
+                            "diffusion k = 1 + x^2, degree-2 rules", "variants": out}
+    finally:
+        s.close()
+
+
+def config_j2(dev, steps=5):
+    """Elastoplastic hex8 (J2 / Voce), 96^3, second load step from the committed first step: the
+    plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules --
+    work stealing, static queues packed by the MLP trained on the stealing run's item timings, and
+    static queues packed by Gauss-point weights."""
+    import torch
+    from paper_1805_03949_gb300 import fea, meshgen as mg
+    from oracle import mlp_oracle
+    amp = json.load(open(os.path.join(ROOT, "tests", "golden", "j2_amplitude.json")))["amplitude"]
+    mesh, U = mg.j2_workload(96, amp)
+    s = fea.System.from_mesh(mesh, 3, device=dev, with_cols=False)
+    try:
+        u = torch.tensor(U.reshape(-1), device=dev)
+        st1 = torch.empty((mesh.n_elems, 8, 7), dtype=torch.float64, device=dev)
+        yl = torch.empty((mesh.n_elems, 8), dtype=torch.uint8, device=dev)
+        s.assemble(fea.make_operator(kind=fea.FEA_OP_J2, precision=0, u=0.5 * u, state_out=st1))
+        st2 = torch.empty_like(st1)
+        base = dict(kind=fea.FEA_OP_J2, u=u, state_in=st1, state_out=st2)
+        out = {}
+        for name, op in (("fp64_per_type", fea.make_operator(precision=0, yield_out=yl, **base)),
+                         ("fp32_per_type", fea.make_operator(precision=1, **base))):
+            ms = _time_calls(lambda: s.assemble(op), steps)
+            s.check()
+            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        yield_frac = float(yl.float().mean().item())
+        chunk = 32
+        types, _, counts = fea.fea_work_items(s.handle, chunk)
+        item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
+        steal = fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
+        ms = _time_calls(lambda: s.assemble(steal), steps)
+        out["fp32_persistent_steal"] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        # the cost model learns from the item timings the stealing run recorded
+        X = fea.fea_item_features(s.handle, chunk, len(counts), u, st1, device=dev)
+        y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
+        h = fea.fea_costmodel_create(6, mlp_oracle.xavier_init(6).astype(np.float32))
+        t0 = time.perf_counter()
+        fea.fea_costmodel_fit_scaler(h, X, y)
+        loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())
+        pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
+        train_s = time.perf_counter() - t0
+        fea.fea_costmodel_destroy(h)
+        grid = fea.fea_persistent_grid(steal, s.handle)
+        for name, cost in (("fp32_persistent_mlp_queues", np.exp(pred) * counts),
+                           ("fp32_persistent_gauss_point_queues",
+                            counts * np.array([4, 8, 6, 8])[types].astype(np.float64))):
+            q, off, _ = fea.fea_pack_lpt(cost, grid)
+            qd, od = torch.tensor(q, device=dev), torch.tensor(off, device=dev)
+            op = fea.make_operator(precision=1, schedule=fea.FEA_SCHED_QUEUES, n_ctas=grid, queue=qd,
+                                   queue_off=od, chunk=chunk, **base)
+            ms = _time_calls(lambda: s.assemble(op), steps)
+            s.check()
+            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        return {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
+                            f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
+                "variants": out, "work_items": len(counts), "chunk": chunk, "grid": grid,
+                "mlp": {"train_loss": loss, "train_s": train_s, "epochs": 600},
+                "mlp_gain_vs_gauss_points": out["fp32_persistent_gauss_point_queues"]["ms"]
+                / out["fp32_persistent_mlp_queues"]["ms"] - 1.0}
+    finally:
+        s.close()
+
+
+def config_batch(dev, steps=10):
+    """256 tet4/hex8 elasticity meshes (log-uniform 1e3..2e5 elements), one graph-captured
+    persistent launch, autotuned chunk and grid; aggregate rate and per-mesh latency."""
+    import torch
+    from paper_1805_03949_gb300 import fea, meshgen as mg
+    meshes = mg.batch_meshes(256, 5)
+    systems = [fea.System.from_mesh(m, 3, device=dev, with_cols=False) for m in meshes]
+    batch = None
+    try:
+        op = fea.make_operator(kind=1, precision=1, poisson=0.3)
+        batch = fea.Batch(op, systems)
+        tuned = batch.autotune(reps=2)
+        batch.capture()
+        ms = _time_calls(batch.assemble, steps)
+        lat = batch.latency_ns().astype(np.float64) * 1e-6
+        for s in systems:
+            s.check()
+        E = sum(m.n_elems for m in meshes)
+        return {"workload": f"256 tet4/hex8 elasticity meshes, {E:,} elements, FP32-integrate, one CUDA graph "
+                            "(zeroing kernel + persistent work-stealing launch)",
+                "ms": ms, "elements_per_s": E / (ms * 1e-3), "autotuned": tuned,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "max": float(lat.max())}}
+    finally:
+        if batch is not None:
+            batch.close()
+        for s in systems:
+            s.close()
+
+
+def other_configs(args, dev):
+    out = {}
+    wanted = [c for c in args.configs.split(",") if c]
+    for key, fn in (("c3", config_hybrid), ("c4", config_j2), ("c5", config_batch)):
+        if key in wanted:
+            t0 = time.perf_counter()
+            out[key] = fn(dev)
+            out[key]["wall_s"] = time.perf_counter() - t0
+            import torch
+            torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -403,8 +554,8 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "hex8 linear elasticity, 128^3 jittered cube (+-0.2h, PCG64 seed 2), "
-                                   "2,097,152 elements, 513,599,625 nonzeros, 2x2x2 Gauss",
+            "config": {"workload": f"hex8 linear elasticity, {args.n}^3 jittered cube (+-0.2h, PCG64 seed 2), "
+                                   f"{E:,} elements, {nnz:,} nonzeros, 2x2x2 Gauss",
                        "sample": f"{args.ref_layers} cell layers ({E} elements) per step"},
             "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.ref_layers} of 128 cell layers per step"},
@@ -425,6 +576,8 @@ def main():
     ap.add_argument("--cpu-layers", type=int, default=8)
     ap.add_argument("--ref-layers", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", default="c3,c4,c5",
+                    help="other workloads timed after the headline one (comma list of c3, c4, c5; '' for none)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

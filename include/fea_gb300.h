@@ -272,6 +272,110 @@ int fea_work_items(const fea_mesh* mesh, int chunk, int64_t* n_items, int32_t* t
  * how many queues a FEA_SCHED_QUEUES packing should fill.  Host call. */
 int fea_persistent_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
 
+/* ---------------------------------------------------------------------------
+ * Learned cost model (the GPU counterpart of the paper's dynamic load
+ * balancing, Sec. 4: element costs are not known a priori).  A small MLP,
+ * n_in features -> 32 tanh -> 32 tanh -> 1, trained by mean squared error and
+ * full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the standardised
+ * features and target (training-set mean and population standard deviation;
+ * a zero deviation is replaced by 1).  All tensors are FP32, device memory,
+ * row-major: X [n][n_in], y [n].  Parameter vector (n_params = 32 n_in + 1,121):
+ * W1 [32][n_in], b1 [32], W2 [32][32], b2 [32], w3 [32], b3.
+ * ------------------------------------------------------------------------- */
+typedef struct fea_costmodel fea_costmodel;
+
+/* New model with the given initial parameters (host, n_params floats);
+ * 1 <= n_in <= 8.  Synchronous. */
+int fea_costmodel_create(int n_in, const float* params_h, fea_costmodel** out);
+int fea_costmodel_destroy(fea_costmodel* model);
+
+/* Current parameters (n_params floats) and scaler (x mean [n_in], x std
+ * [n_in], y mean, y std); either pointer may be NULL.  Synchronous. */
+int fea_costmodel_get_params(const fea_costmodel* model, float* params_h, float* scaler_h);
+
+/* Fit the scaler to a training set.  Stream-ordered. */
+int fea_costmodel_fit_scaler(fea_costmodel* model, const float* X_d, const float* y_d, int64_t n, void* stream);
+
+/* Full-batch gradient (grad_d [n_params]) and loss (loss_d [1], may be NULL)
+ * at the current parameters, no update.  Stream-ordered. */
+int fea_costmodel_grad(fea_costmodel* model, const float* X_d, const float* y_d, int64_t n, float* grad_d,
+                       float* loss_d, void* stream);
+
+/* `epochs` full-batch Adam steps with learning rate lr; loss_d (may be NULL)
+ * receives the loss of the last epoch before its update.  Stream-ordered. */
+int fea_costmodel_train(fea_costmodel* model, const float* X_d, const float* y_d, int64_t n, int epochs, float lr,
+                        float* loss_d, void* stream);
+
+/* Predictions in target units, y_d [n].  Stream-ordered. */
+int fea_costmodel_predict(const fea_costmodel* model, const float* X_d, int64_t n, float* y_d, void* stream);
+
+/* Features of the work items of fea_work_items(mesh, chunk): X_d [n_items][6]
+ * float = per item, the mean over its elements of the one-hot element type
+ * (4), the fraction of the element's Gauss points whose committed equivalent
+ * plastic strain (state_in_d, fea_operator layout) is positive, and the
+ * Frobenius norm of sym(grad u) (u_d [n_nodes][3]) at the element's reference
+ * centroid.  u_d and state_in_d may be NULL (feature 0).  Synchronous. */
+int fea_item_features(fea_mesh* mesh, int chunk, const double* u_d, const double* state_in_d, float* X_d,
+                      void* stream);
+
+/* Longest-processing-time-first packing (Graham 1969) of n_items items with
+ * costs cost_h into n_queues queues: items in decreasing cost (ties: lower id
+ * first), each onto the queue with the least load so far (ties: lower queue).
+ * Output, host: queue_h [n_items] item ids queue by queue in assignment order,
+ * queue_off_h [n_queues + 1], load_h [n_queues] (may be NULL).  The result
+ * feeds FEA_SCHED_QUEUES.  Host call. */
+int fea_pack_lpt(const double* cost_h, int64_t n_items, int n_queues, int32_t* queue_h, int64_t* queue_off_h,
+                 double* load_h);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent meshes of uneven sizes assembled by one
+ * persistent launch (a zeroing kernel, then CTAs that take work items of any
+ * (mesh, element type) by work stealing), optionally captured once as a CUDA
+ * graph and replayed.  Each entry names a mesh whose pattern and map were
+ * built for the operator's ndof and the caller-owned device buffers of its
+ * system; they must stay valid for the life of the batch.
+ * ------------------------------------------------------------------------- */
+typedef struct fea_batch fea_batch;
+
+typedef struct {
+  fea_mesh* mesh;
+  const int64_t* row_ptr_d;
+  const int32_t* node_map_d;
+  double* A_d;  /* overwritten by every fea_batch_assemble */
+  double* b_d;
+} fea_batch_entry;
+
+/* op: FEA_OP_DIFFUSION or FEA_OP_ELASTICITY (schedule and scatter fields are
+ * ignored: the batch always uses work stealing and the ATOMIC scatter);
+ * op->chunk (0 = 128) and op->n_ctas (0 = resident CTAs) give the initial
+ * configuration.  1 <= n_meshes <= 32767.  Synchronous. */
+int fea_batch_create(const fea_operator* op, int n_meshes, const fea_batch_entry* entries_h, fea_batch** out);
+int fea_batch_destroy(fea_batch* batch);
+
+/* Change the work-item size and grid (synchronizes the device; drops a
+ * captured graph). */
+int fea_batch_set_config(fea_batch* batch, int chunk, int n_ctas);
+
+/* Items, chunk size and grid of the current configuration.  Host call. */
+int fea_batch_info(const fea_batch* batch, int64_t* n_items, int* chunk, int* grid);
+
+/* Time chunk sizes 16..512 and grids of k x SM-count CTAs up to the resident
+ * count (median of reps runs each, CUDA events on stream), keep the fastest
+ * and return it.  Synchronous; the batch's systems are overwritten. */
+int fea_batch_autotune(fea_batch* batch, int reps, void* stream, int* chunk_out, int* n_ctas_out, float* ms_out);
+
+/* Capture one assembly of the batch as a CUDA graph (on an internal stream);
+ * later fea_batch_assemble calls replay it.  Synchronous. */
+int fea_batch_capture(fea_batch* batch, void* stream);
+
+/* Assemble every system of the batch (overwrite semantics).  Stream-ordered. */
+int fea_batch_assemble(fea_batch* batch, void* stream);
+
+/* Per-mesh latency of the last assembly, ns: the %globaltimer at which the
+ * mesh's last work item finished minus the start of the persistent launch.
+ * Synchronizes the stream. */
+int fea_batch_latency(fea_batch* batch, uint64_t* mesh_ns_h, void* stream);
+
 /* CSR row pointers from row lengths, allocating nothing on the device.
  * The paper has no counterpart: this is a service for callers that cannot let
  * a library allocate device memory -- applications that reserve all of the

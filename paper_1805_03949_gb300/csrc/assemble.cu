@@ -547,6 +547,8 @@ __constant__ RefRule c_rules[kNumRules];
 struct PersistAsmArgs {
   AsmParams table[kNumTypes];  // entry t: the group of element type t
   int32_t slot[kNumTypes];     // its quadrature rule
+  const AsmParams* tab;        // batches: device table of every (mesh, type) entry (overrides table)
+  const int32_t* tab_slot;     // batches: rule slot per entry
   SchedArgs S;
 };
 
@@ -574,22 +576,23 @@ __global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ Pers
   constexpr int S2 = PersistCfg<OP, PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_smem[];
   __shared__ int s_item;
+  sched_start(A.S);
   int k = 0;
   for (;;) {
     const int item = sched_next(A.S, k, &s_item);
     if (item < 0) break;
     const uint64_t t0 = global_ns();
     const WorkItem it = A.S.items[item];
-    const AsmParams& P = A.table[it.entry];
+    const AsmParams& P = A.tab ? A.tab[it.entry] : A.table[it.entry];
     const int64_t first = it.first, end = (int64_t)it.first + it.count;
-    switch (A.slot[it.entry]) {
+    switch (A.tab ? A.tab_slot[it.entry] : A.slot[it.entry]) {
       case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
       case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
       case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
       case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
       default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
     }
-    sched_record(A.S, item, t0);
+    sched_record(A.S, item, it.entry, t0);
   }
 }
 
@@ -656,6 +659,38 @@ static int launch_persistent_t(const PersistAsmArgs& args, int n_ctas, bool dry,
     FEA_CUDA(cudaGetLastError());
   }
   return FEA_OK;
+}
+
+// Persistent launch over a device table of (mesh, type) entries (batches).
+int launch_persistent_batch(const fea_operator* op, const void* tab, const int32_t* tab_slot, const SchedArgs& S,
+                            int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
+  PersistAsmArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.tab = static_cast<const AsmParams*>(tab);
+  args.tab_slot = tab_slot;
+  args.S = S;
+  const bool f64 = op->precision == FEA_FP64;
+  if (op->kind == FEA_OP_DIFFUSION)
+    return f64 ? launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP64>(args, n_ctas, dry, s, grid_out)
+               : launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+  return f64 ? launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP64>(args, n_ctas, dry, s, grid_out)
+             : launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+}
+
+// Size in bytes of one entry of the batch table, and the table entry of
+// (mesh handle, type t) for the operator (host side, written into a buffer).
+size_t batch_entry_bytes() { return sizeof(AsmParams); }
+
+void batch_entry(const fea_operator* op, fea_mesh* m, int t, const int64_t* row_ptr, const int32_t* node_map,
+                 double* A, double* b, void* out, int32_t* slot) {
+  AsmParams P = base_params(op, m, row_ptr, node_map, A, b);
+  const TypeGroup& g = m->group[t];
+  P.tconn = g.conn;
+  P.ids = g.ids;
+  P.mapoff = g.mapoff;
+  P.n = g.n;
+  std::memcpy(out, &P, sizeof(P));
+  *slot = rule_slot_of(t, op->tet_rule);
 }
 
 // Persistent launch of the diffusion / elasticity tile over every type group.

@@ -128,6 +128,11 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
                         double* A, double* b, cudaStream_t s);
 int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
                 double* b, cudaStream_t s);
+int launch_persistent_batch(const fea_operator* op, const void* tab, const int32_t* tab_slot, const SchedArgs& S,
+                            int n_ctas, bool dry, cudaStream_t s, int* grid_out);
+size_t batch_entry_bytes();
+void batch_entry(const fea_operator* op, fea_mesh* m, int t, const int64_t* row_ptr, const int32_t* node_map,
+                 double* A, double* b, void* out, int32_t* slot);
 int init_rule_constants();     // __constant__ quadrature tables of the persistent kernels (current device)
 int init_rule_constants_j2();
 void free_sched(fea_mesh* m);

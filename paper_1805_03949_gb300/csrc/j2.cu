@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ P
   constexpr int S2 = PersistJ2Cfg<PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_j2_smem[];
   __shared__ int s_item;
+  sched_start(A.S);
   int k = 0;
   for (;;) {
     const int item = sched_next(A.S, k, &s_item);
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ P
       case kRuleHex8: persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, P, first, end); break;
       default: persist_j2_item<FEA_TET4, kRuleTet4, PREC, 1>(persist_j2_smem, P, first, end); break;
     }
-    sched_record(A.S, item, t0);
+    sched_record(A.S, item, it.entry, t0);
   }
 }
 

@@ -34,6 +34,11 @@ struct SchedArgs {
   const int64_t* queue_off;
   uint64_t* item_ns;      // optional per-item duration
   int32_t* item_cta;      // optional per-item CTA
+  // batches of meshes (entry = 4 * mesh + type): items left per mesh, the
+  // %globaltimer at which each mesh's last item finished, and the launch start
+  int32_t* mesh_left;
+  uint64_t* mesh_done_ns;
+  unsigned long long* start_ns;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -66,11 +71,22 @@ __device__ __forceinline__ int sched_next(const SchedArgs& S, int& k, int* s_ite
   return item;
 }
 
-__device__ __forceinline__ void sched_record(const SchedArgs& S, int item, uint64_t t0) {
+// Called by every thread after the item's work (and a barrier).
+__device__ __forceinline__ void sched_record(const SchedArgs& S, int item, int entry, uint64_t t0) {
   if (threadIdx.x == 0) {
-    if (S.item_ns) S.item_ns[item] = global_ns() - t0;
+    const uint64_t t1 = global_ns();
+    if (S.item_ns) S.item_ns[item] = t1 - t0;
     if (S.item_cta) S.item_cta[item] = (int32_t)blockIdx.x;
+    if (S.mesh_left) {
+      __threadfence();
+      if (atomicSub(&S.mesh_left[entry >> 2], 1) == 1 && S.mesh_done_ns) S.mesh_done_ns[entry >> 2] = t1;
+    }
   }
+}
+
+// launch start of a batch: the earliest CTA start
+__device__ __forceinline__ void sched_start(const SchedArgs& S) {
+  if (threadIdx.x == 0 && S.start_ns) atomicMin(S.start_ns, (unsigned long long)global_ns());
 }
 
 }  // namespace fea

@@ -48,6 +48,11 @@ class fea_mesh_desc(ctypes.Structure):
                 ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class fea_batch_entry(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("row_ptr_d", ctypes.c_void_p), ("node_map_d", ctypes.c_void_p),
+                ("A_d", ctypes.c_void_p), ("b_d", ctypes.c_void_p)]
+
+
 class fea_operator(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("precision", ctypes.c_int32), ("scatter", ctypes.c_int32),
                 ("tet_rule", ctypes.c_int32), ("k0", ctypes.c_double), ("k2", ctypes.c_double),
@@ -92,6 +97,15 @@ def _load():
         "fea_costmodel_predict": (I32, [P, P, I64, P, P]),
         "fea_item_features": (I32, [P, I32, P, P, P, P]),
         "fea_pack_lpt": (I32, [P, I64, I32, P, P, P]),
+        "fea_batch_create": (I32, [ctypes.POINTER(fea_operator), I32, P, ctypes.POINTER(P)]),
+        "fea_batch_destroy": (I32, [P]),
+        "fea_batch_set_config": (I32, [P, I32, I32]),
+        "fea_batch_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "fea_batch_autotune": (I32, [P, I32, P, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                     ctypes.POINTER(ctypes.c_float)]),
+        "fea_batch_capture": (I32, [P, P]),
+        "fea_batch_assemble": (I32, [P, P]),
+        "fea_batch_latency": (I32, [P, P, P]),
         "fea_persistent_grid": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_mesh_set_rows_block": (I32, [P, I32]),
         "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
@@ -320,6 +334,57 @@ def fea_pack_lpt(costs, n_queues: int):
     load = np.zeros(n_queues, dtype=np.float64)
     _check(_lib.fea_pack_lpt(_np_ptr(c), len(c), n_queues, _np_ptr(q), _np_ptr(off), _np_ptr(load)))
     return q, off, load
+
+
+# ---------------------------------------------------------------------------
+# batches of meshes (batch.cu)
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many Systems assembled by one persistent launch (optionally a CUDA graph)."""
+
+    def __init__(self, op: "fea_operator", systems):
+        self.systems = list(systems)
+        arr = (fea_batch_entry * len(self.systems))()
+        for k, s in enumerate(self.systems):
+            arr[k].mesh = s.handle
+            arr[k].row_ptr_d = s.row_ptr.data_ptr()
+            arr[k].node_map_d = s.node_map.data_ptr()
+            arr[k].A_d = s.A.data_ptr()
+            arr[k].b_d = s.b.data_ptr()
+        self.handle = ctypes.c_void_p()
+        _check(_lib.fea_batch_create(ctypes.byref(op), len(self.systems), arr, ctypes.byref(self.handle)))
+
+    def set_config(self, chunk: int, n_ctas: int):
+        _check(_lib.fea_batch_set_config(self.handle, chunk, n_ctas))
+
+    def info(self):
+        n, c, g = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.fea_batch_info(self.handle, ctypes.byref(n), ctypes.byref(c), ctypes.byref(g)))
+        return dict(items=n.value, chunk=c.value, grid=g.value)
+
+    def autotune(self, reps: int = 3, stream=None):
+        c, g, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        _check(_lib.fea_batch_autotune(self.handle, reps, _stream(stream), ctypes.byref(c), ctypes.byref(g),
+                                       ctypes.byref(ms)))
+        return dict(chunk=c.value, grid=g.value, ms=ms.value)
+
+    def capture(self, stream=None):
+        _check(_lib.fea_batch_capture(self.handle, _stream(stream)))
+
+    def assemble(self, stream=None):
+        _check(_lib.fea_batch_assemble(self.handle, _stream(stream)))
+
+    def latency_ns(self, stream=None):
+        import numpy as np
+        out = np.zeros(len(self.systems), dtype=np.uint64)
+        _check(_lib.fea_batch_latency(self.handle, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(_lib.fea_batch_destroy(self.handle))
+            self.handle = None
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:
