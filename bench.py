@@ -146,6 +146,25 @@ def record_bytes(n_elems):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing (one replica per rank, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it); identity on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -234,10 +253,7 @@ def run_ours(args, rank, world, local_rank):
         geo_ms = mean([evs[1].elapsed_time(evs[-2]) for evs in ev_steps]) if nk > 1 and "color" not in name else 0.0
         fea.set_events(op, None)
         sysm.check()
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         results[name] = dict(ms_per_step=total_ms / steps, kernel_ms=kern_ms, zero_ms=zero_ms, main_ms=main_ms,
                              geo_ms=geo_ms, launches=nk, steps=steps)
     clk = clocks.stop()
@@ -271,10 +287,7 @@ def run_ours(args, rank, world, local_rank):
     s1.record()
     torch.cuda.synchronize()
     e2e_ms = s0.elapsed_time(s1) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     sysm.check()
 
     if rank == 0:
@@ -314,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
         roof.update(frac=roof["achieved"] / roof["peak"], traffic=None, kernel=k_name, kernel_ms=k_ms)
         line = {
             "metric": METRIC,
-            "value": world * E / (r["ms_per_step"] * 1e-3),
+            "value": whole_job_rate(E, world, r["ms_per_step"]),
             "unit": "elements/s",
             "n_gpus": world,
             "steps": r["steps"],
@@ -381,36 +394,70 @@ def _time_calls(fn, steps, warmup=2):
     return float(statistics.median(ts))
 
 
+def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk):
+    """Persistent schedules of one workload: work stealing (whose per-item timings train the
+    cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, and
+    the same queues with stealing as the fallback once a CTA's own queue is empty."""
+    import torch
+    from oracle import mlp_oracle
+    item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
+    steal = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
+    out = {"persistent_steal": _time_calls(lambda: s.assemble(steal), steps)}
+    s.check()
+    y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
+    h = fea.fea_costmodel_create(6, mlp_oracle.xavier_init(6).astype(np.float32))
+    t0 = time.perf_counter()
+    fea.fea_costmodel_fit_scaler(h, X, y)
+    loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())
+    pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
+    train_s = time.perf_counter() - t0
+    fea.fea_costmodel_destroy(h)
+    grid = fea.fea_persistent_grid(steal, s.handle)
+    costs = {"mlp": np.exp(pred) * counts,
+             "gauss_points": counts * np.array([4, 8, 6, 8])[types].astype(np.float64)}
+    for name, cost in costs.items():
+        q, off, _ = fea.fea_pack_lpt(cost, grid)
+        qd, od = torch.tensor(q, device=dev), torch.tensor(off, device=dev)
+        for mode, suffix in ((fea.FEA_SCHED_QUEUES, ""), (fea.FEA_SCHED_QUEUES_STEAL, "_steal")):
+            op = fea.make_operator(schedule=mode, n_ctas=grid, queue=qd, queue_off=od, chunk=chunk, **base)
+            out[f"{name}_queues{suffix}"] = _time_calls(lambda: s.assemble(op), steps)
+            s.check()
+    return out, {"train_loss": loss, "train_s": train_s, "epochs": 600, "items": len(counts), "chunk": chunk,
+                 "grid": grid,
+                 "gain_static": out["gauss_points_queues"] / out["mlp_queues"] - 1.0,
+                 "gain_with_steal": out["gauss_points_queues_steal"] / out["mlp_queues_steal"] - 1.0}
+
+
 def config_hybrid(dev, steps=5):
     """Hybrid tet/pyramid/prism/hex diffusion, k = 1 + x^2, degree-2 rules: per-type launches
-    against one persistent launch over every type (work stealing)."""
+    against one persistent launch over every type, scheduled by stealing or by packed queues."""
     from paper_1805_03949_gb300 import fea, meshgen as mg
     mesh = mg.hybrid_cube(100, 3)
     s = fea.System.from_mesh(mesh, 1, device=dev, with_cols=False)
     try:
         kw = dict(kind=0, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
-        ops = {"fp64_per_type": fea.make_operator(precision=0, **kw),
-               "fp32_per_type": fea.make_operator(precision=1, **kw),
-               "fp32_persistent_steal": fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, **kw)}
         out = {}
-        for name, op in ops.items():
-            ms = _time_calls(lambda: s.assemble(op), steps)
+        for name, op in (("fp64_per_type", fea.make_operator(precision=0, **kw)),
+                         ("fp32_per_type", fea.make_operator(precision=1, **kw))):
+            out[name] = _time_calls(lambda: s.assemble(op), steps)
             s.check()
-            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        chunk = 128
+        types, _, counts = fea.fea_work_items(s.handle, chunk)
+        X = fea.fea_item_features(s.handle, chunk, len(counts), device=dev)
+        sched, mlp = schedule_study(fea, s, dict(precision=1, **kw), counts, types, X, dev, steps, chunk)
+        out.update({"fp32_" + k: v for k, v in sched.items()})
         return {"workload": "hybrid 100^3 cube, 4,528,302 elements (tet 40 / pyr 10 / prism 20 / hex 30 %), "
-                            "diffusion k = 1 + x^2, degree-2 rules", "variants": out}
+                            "diffusion k = 1 + x^2, degree-2 rules",
+                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp}
     finally:
         s.close()
 
 
 def config_j2(dev, steps=5):
     """Elastoplastic hex8 (J2 / Voce), 96^3, second load step from the committed first step: the
-    plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules --
-    work stealing, static queues packed by the MLP trained on the stealing run's item timings, and
-    static queues packed by Gauss-point weights."""
+    plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules."""
     import torch
     from paper_1805_03949_gb300 import fea, meshgen as mg
-    from oracle import mlp_oracle
     amp = json.load(open(os.path.join(ROOT, "tests", "golden", "j2_amplitude.json")))["amplitude"]
     mesh, U = mg.j2_workload(96, amp)
     s = fea.System.from_mesh(mesh, 3, device=dev, with_cols=False)
@@ -424,43 +471,17 @@ def config_j2(dev, steps=5):
         out = {}
         for name, op in (("fp64_per_type", fea.make_operator(precision=0, yield_out=yl, **base)),
                          ("fp32_per_type", fea.make_operator(precision=1, **base))):
-            ms = _time_calls(lambda: s.assemble(op), steps)
+            out[name] = _time_calls(lambda: s.assemble(op), steps)
             s.check()
-            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
         yield_frac = float(yl.float().mean().item())
         chunk = 32
         types, _, counts = fea.fea_work_items(s.handle, chunk)
-        item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
-        steal = fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
-        ms = _time_calls(lambda: s.assemble(steal), steps)
-        out["fp32_persistent_steal"] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
-        # the cost model learns from the item timings the stealing run recorded
         X = fea.fea_item_features(s.handle, chunk, len(counts), u, st1, device=dev)
-        y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
-        h = fea.fea_costmodel_create(6, mlp_oracle.xavier_init(6).astype(np.float32))
-        t0 = time.perf_counter()
-        fea.fea_costmodel_fit_scaler(h, X, y)
-        loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())
-        pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
-        train_s = time.perf_counter() - t0
-        fea.fea_costmodel_destroy(h)
-        grid = fea.fea_persistent_grid(steal, s.handle)
-        for name, cost in (("fp32_persistent_mlp_queues", np.exp(pred) * counts),
-                           ("fp32_persistent_gauss_point_queues",
-                            counts * np.array([4, 8, 6, 8])[types].astype(np.float64))):
-            q, off, _ = fea.fea_pack_lpt(cost, grid)
-            qd, od = torch.tensor(q, device=dev), torch.tensor(off, device=dev)
-            op = fea.make_operator(precision=1, schedule=fea.FEA_SCHED_QUEUES, n_ctas=grid, queue=qd,
-                                   queue_off=od, chunk=chunk, **base)
-            ms = _time_calls(lambda: s.assemble(op), steps)
-            s.check()
-            out[name] = {"ms": ms, "elements_per_s": mesh.n_elems / (ms * 1e-3)}
+        sched, mlp = schedule_study(fea, s, dict(precision=1, **base), counts, types, X, dev, steps, chunk)
+        out.update({"fp32_" + k: v for k, v in sched.items()})
         return {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
                             f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
-                "variants": out, "work_items": len(counts), "chunk": chunk, "grid": grid,
-                "mlp": {"train_loss": loss, "train_s": train_s, "epochs": 600},
-                "mlp_gain_vs_gauss_points": out["fp32_persistent_gauss_point_queues"]["ms"]
-                / out["fp32_persistent_mlp_queues"]["ms"] - 1.0}
+                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp}
     finally:
         s.close()
 

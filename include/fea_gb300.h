@@ -105,12 +105,17 @@ typedef enum {
  * cut into ceil(n_t / chunk) items (fea_work_items lists them). */
 typedef enum {
   FEA_SCHED_PER_TYPE = 0, /* one launch per element type (per color class for FEA_SCATTER_COLOR) */
-  FEA_SCHED_STEAL = 1,    /* one persistent launch over every type: n_ctas CTAs take items in list
-                             order from a global counter (dynamic work stealing) */
-  FEA_SCHED_QUEUES = 2    /* one persistent launch: CTA c processes exactly the items
+  FEA_SCHED_STEAL = 1,    /* one persistent launch over every type: n_ctas CTAs take items from a
+                             global counter (dynamic work stealing), in list order, or in the order
+                             queue_d gives when queue_d is set and queue_off_d is NULL (a permutation
+                             of all items, e.g. by decreasing predicted cost) */
+  FEA_SCHED_QUEUES = 2,   /* one persistent launch: CTA c processes exactly the items
                              queue_d[queue_off_d[c] .. queue_off_d[c+1]) in that order (static
                              queues packed by the caller, e.g. longest-processing-time first on
                              predicted costs); no stealing */
+  FEA_SCHED_QUEUES_STEAL = 3 /* as FEA_SCHED_QUEUES, then a CTA whose queue is empty takes the
+                             next item of the other queues (c+1, c+2, ... in turn), so the static
+                             packing is the plan and stealing corrects what it mispredicted */
 } fea_schedule;
 
 /* Mesh description for fea_mesh_upload.  coords is xyz per node (AoS,
@@ -144,8 +149,8 @@ typedef struct {
  *             launches (only those with index < n_events are recorded).
  *  schedule   fea_schedule (FEA_SCATTER_ATOMIC only for the persistent ones)
  *  chunk      elements per work item (persistent schedules; 0 = 128)
- *  n_ctas     persistent grid size (0 = 2 CTAs per SM); FEA_SCHED_QUEUES needs it
- *  queue_d, queue_off_d  FEA_SCHED_QUEUES: int32 item ids and int64 [n_ctas + 1]
+ *  n_ctas     persistent grid size (0 = the resident-CTA count); the queue schedules need it
+ *  queue_d, queue_off_d  FEA_SCHED_QUEUES*: int32 item ids and int64 [n_ctas + 1]
  *             offsets (device); every item must appear exactly once (not checked)
  *  item_ns_d  optional uint64 [n_items] (device): per item, the %globaltimer
  *             nanoseconds its CTA spent on it (persistent schedules)

@@ -220,8 +220,8 @@ __device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int
   cofactors(J, C);
   const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
   if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
-  const double wd = rr.w[q] * det * (1.0 / (s * s * s));
   if constexpr (std::is_same<R, double>::value) {
+    const double wd = rr.w[q] * det * (1.0 / (s * s * s));
     const double inv = s / det;
 #pragma unroll
     for (int a = 0; a < NN; ++a)
@@ -239,14 +239,15 @@ __device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Cf[i][j] = (float)C[i][j];
-    const float inv = (float)s / (float)det;
+      for (int j = 0; j < 3; ++j) Cf[i][j] = f64_to_f32_rn(C[i][j]);
+    const float detf = f64_to_f32_rn(det);
+    const float inv = (float)s / detf;
 #pragma unroll
     for (int a = 0; a < NN; ++a)
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         sm.G[le][q][a][i] = (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * inv;
-    const float wdf = (float)wd;
+    const float wdf = rr.wf[q] * detf * (float)(1.0 / (s * s * s));
     sm.W[le][q] = wdf;
     if constexpr (OP == FEA_OP_DIFFUSION) {
       const float x = (float)xq;
@@ -379,8 +380,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
         const int a = hex8_corner_node(p);
         double v[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] - sm.X[le][0][i] : 0.0;
-        const double x0 = valid ? sm.X[le][0][0] : 0.0;
+        for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] : 0.0;
         hex8_modal(v);
         __syncwarp();
 #pragma unroll
@@ -397,7 +397,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
             double acc = 0.0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc = fma(sm.X[le][k][0], m[k], acc);
-            xq = x0 + 0.125 * acc;
+            xq = 0.125 * acc;
           }
           geometry_finish<OP, NN>(sm, rr, le, p, original_id(P, et), J, 8.0, xq, P);
         }
@@ -534,7 +534,8 @@ __device__ __forceinline__ void tile_body(typename TileCfg<TYPE, SLOT, OP, PREC,
 template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
 __global__ void __launch_bounds__(128) k_assemble_tile(const __grid_constant__ RefRule rr,
                                                        const __grid_constant__ AsmParams P) {
-  __shared__ typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem sm;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  auto& sm = *reinterpret_cast<typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem*>(tile_smem);
   tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC>(sm, rr, P, (int64_t)blockIdx.x * TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::EPC,
                                              P.n);
 }
@@ -571,7 +572,9 @@ __device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams
     tile_body<TYPE, SLOT, OP, PREC, SPLIT, FEA_SCATTER_ATOMIC>(sm, c_rules[SLOT], P, e0, end);
 }
 
-template <int OP, int PREC>
+// ONLY >= 0: every item uses that rule slot (a single-type mesh), so the
+// kernel holds one tile body and its register budget; -1: any element type
+template <int OP, int PREC, int ONLY>
 __global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ PersistAsmArgs A) {
   constexpr int S2 = PersistCfg<OP, PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_smem[];
@@ -583,14 +586,30 @@ __global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ Pers
     if (item < 0) break;
     const uint64_t t0 = global_ns();
     const WorkItem it = A.S.items[item];
-    const AsmParams& P = A.tab ? A.tab[it.entry] : A.table[it.entry];
     const int64_t first = it.first, end = (int64_t)it.first + it.count;
-    switch (A.tab ? A.tab_slot[it.entry] : A.slot[it.entry]) {
-      case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
-      case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
-      case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
-      case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
-      default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
+    // single mesh: entry t is type t, read at a constant offset of the
+    // parameter space; batches: the device table
+    if constexpr (ONLY == kRuleHex8) {
+      persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, A.table[FEA_HEX8], first, end);
+    } else if (A.tab) {
+      const AsmParams& P = A.tab[it.entry];
+      switch (A.tab_slot[it.entry]) {
+        case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
+        default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
+      }
+    } else {
+      switch (A.slot[it.entry]) {
+        case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
+        case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
+        case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, A.table[FEA_PYR5], first, end); break;
+        case kRulePrism6:
+          persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, A.table[FEA_PRISM6], first, end);
+          break;
+        default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, A.table[FEA_HEX8], first, end); break;
+      }
     }
     sched_record(A.S, item, it.entry, t0);
   }
@@ -640,10 +659,12 @@ static int rule_slot_of(int type, int tet_rule) {
   }
 }
 
-template <int OP, int PREC>
-static int launch_persistent_t(const PersistAsmArgs& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
-  constexpr size_t smem = PersistCfg<OP, PREC>::smem;
-  auto kern = k_persistent<OP, PREC>;
+template <int OP, int PREC, int ONLY>
+static int launch_persistent_k(const PersistAsmArgs& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
+  constexpr size_t smem = ONLY == kRuleHex8 ? sizeof(typename TileCfg<FEA_HEX8, kRuleHex8, OP, PREC,
+                                                                       PersistCfg<OP, PREC>::S2>::Smem)
+                                            : PersistCfg<OP, PREC>::smem;
+  auto kern = k_persistent<OP, PREC, ONLY>;
   if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = n_ctas;
   if (grid <= 0) {
@@ -659,6 +680,14 @@ static int launch_persistent_t(const PersistAsmArgs& args, int n_ctas, bool dry,
     FEA_CUDA(cudaGetLastError());
   }
   return FEA_OK;
+}
+
+// the hex-only kernel when every item is a 2x2x2 hex, else the generic one
+template <int OP, int PREC>
+static int launch_persistent_t(const PersistAsmArgs& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out,
+                               bool hex_only = false) {
+  return hex_only ? launch_persistent_k<OP, PREC, kRuleHex8>(args, n_ctas, dry, s, grid_out)
+                  : launch_persistent_k<OP, PREC, -1>(args, n_ctas, dry, s, grid_out);
 }
 
 // Persistent launch over a device table of (mesh, type) entries (batches).
@@ -712,14 +741,18 @@ int launch_persistent_assemble(const fea_operator* op, fea_mesh* m, const int64_
     args.slot[t] = rule_slot_of(t, op->tet_rule);
   }
   args.S = S;
+  // a mesh of hexes only runs the single-type kernel
+  bool hex_only = m->group[FEA_HEX8].n > 0;
+  for (int t = 0; t < kNumTypes; ++t)
+    if (t != FEA_HEX8 && m->group[t].n) hex_only = false;
   int rc;
   const bool f64 = op->precision == FEA_FP64;
   if (op->kind == FEA_OP_DIFFUSION)
-    rc = f64 ? launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP64>(args, n_ctas, dry, s, grid_out)
-             : launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+    rc = f64 ? launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP64>(args, n_ctas, dry, s, grid_out, hex_only)
+             : launch_persistent_t<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out, hex_only);
   else
-    rc = f64 ? launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP64>(args, n_ctas, dry, s, grid_out)
-             : launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+    rc = f64 ? launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP64>(args, n_ctas, dry, s, grid_out, hex_only)
+             : launch_persistent_t<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out, hex_only);
   return rc;
 }
 
@@ -730,7 +763,10 @@ template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC>
 static int launch_tile(const AsmParams& P, cudaStream_t s) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   const unsigned grid = grid_for(P.n, Cfg::EPC);
-  k_assemble_tile<TYPE, SLOT, OP, PREC, SPLIT, SC><<<grid, Cfg::THREADS, 0, s>>>(host_rule(SLOT), P);
+  constexpr size_t smem = sizeof(typename Cfg::Smem);
+  auto kern = k_assemble_tile<TYPE, SLOT, OP, PREC, SPLIT, SC>;
+  if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, Cfg::THREADS, smem, s>>>(host_rule(SLOT), P);
   FEA_CUDA(cudaGetLastError());
   return FEA_OK;
 }
@@ -768,7 +804,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_ROWS)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown scatter variant");
   if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
-  if (op->schedule < FEA_SCHED_PER_TYPE || op->schedule > FEA_SCHED_QUEUES)
+  if (op->schedule < FEA_SCHED_PER_TYPE || op->schedule > FEA_SCHED_QUEUES_STEAL)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown schedule");
   const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
   if (m->pattern_ndof != D || !m->pattern_built)

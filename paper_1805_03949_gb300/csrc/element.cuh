@@ -133,7 +133,8 @@ __host__ __device__ constexpr int hex8_corner_node(int p) {
 }
 
 // Lane p of an aligned group of 8 lanes holds the coordinates of corner p on
-// entry and c_p on exit.  Every lane of the warp must call it.
+// entry and c_p on exit (one FP64 add per stage and component: the partner's
+// value enters with the sign of the stage).  Every lane of the warp must call it.
 __device__ __forceinline__ void hex8_modal(double v[3]) {
   const int p = threadIdx.x & 7;
 #pragma unroll
@@ -142,22 +143,44 @@ __device__ __forceinline__ void hex8_modal(double v[3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double o = __shfl_xor_sync(0xffffffffu, v[i], bit);
-      v[i] = (p & bit) ? v[i] - o : v[i] + o;
+      v[i] += (p & bit) ? -o : o;
     }
   }
 }
 
-// J' = 8 J at Gauss point q (xi_s = +-1/sqrt(3) by bit s of q) from c[k][i].
+// J' = 8 J at Gauss point q (xi_s = +-1/sqrt(3) by bit s of q) from c[k][i];
+// the coordinate products are +-1/3 (the rounded square of the point), chosen
+// by sign so that they cost no FP64 multiply.
 __device__ __forceinline__ void hex8_jacobian(const double (*c)[3], int q, double J[3][3]) {
-  const double g = 0.57735026918962576451;
+  constexpr double g = 0.57735026918962576451;
+  constexpr double g2 = g * g;
   const double x = (q & 1) ? g : -g, y = (q & 2) ? g : -g, z = (q & 4) ? g : -g;
-  const double xy = x * y, xz = x * z, yz = y * z;
+  const double xy = ((q ^ (q >> 1)) & 1) ? -g2 : g2;
+  const double xz = ((q ^ (q >> 2)) & 1) ? -g2 : g2;
+  const double yz = (((q >> 1) ^ (q >> 2)) & 1) ? -g2 : g2;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     J[i][0] = fma(c[7][i], yz, fma(c[5][i], z, fma(c[3][i], y, c[1][i])));
     J[i][1] = fma(c[7][i], xz, fma(c[6][i], z, fma(c[3][i], x, c[2][i])));
     J[i][2] = fma(c[7][i], xy, fma(c[6][i], y, fma(c[5][i], x, c[4][i])));
   }
+}
+
+// FP64 -> FP32, rounded to nearest even, with integer instructions (IEEE 754
+// binary64 to binary32): the 52-bit significand keeps its top 23 bits and
+// rounds up when the 29 dropped bits exceed half an ulp, or equal it with an
+// odd kept part; a carry out of the significand moves into the exponent,
+// which also gives the correct overflow to infinity.  Results outside the
+// normal binary32 range, zeros, infinities and NaNs take the hardware
+// conversion.  On GB300 the hardware conversion issues on the FP64 unit.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
+  if (E <= 0 || E >= 255) return (float)x;
+  const uint32_t kept = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1fffffffu;
+  const uint32_t up = (rest > 0x10000000u) || (rest == 0x10000000u && (kept & 1u));
+  return __uint_as_float(((hi & 0x80000000u) | ((uint32_t)E << 23) | kept) + up);
 }
 
 __device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {

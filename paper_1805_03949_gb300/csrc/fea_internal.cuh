@@ -86,6 +86,8 @@ struct fea_mesh {
   std::vector<fea::WorkItem> items_h;
   fea::WorkItem* items = nullptr;               // device copy of items_h
   int32_t* sched_counter = nullptr;             // FEA_SCHED_STEAL counter
+  int32_t* sched_heads = nullptr;               // FEA_SCHED_QUEUES_STEAL queue heads
+  int sched_heads_n = 0;
 };
 
 namespace fea {

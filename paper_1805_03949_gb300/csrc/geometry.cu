@@ -56,8 +56,8 @@ __device__ __forceinline__ void geo_finish(const RefRule& rr, const GeoArgs& P, 
     latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)id);
     return;
   }
-  const double wd = rr.w[q] * det * (1.0 / (s * s * s));
   if constexpr (PREC == FEA_FP64) {
+    const double wd = rr.w[q] * det * (1.0 / (s * s * s));
     double* rec = static_cast<double*>(recp);
     const double sc = sqrt(wd) * s / det;
 #pragma unroll
@@ -68,15 +68,17 @@ __device__ __forceinline__ void geo_finish(const RefRule& rr, const GeoArgs& P, 
     rec[kRecW + q] = wd;
     if (P.diffusion) rec[kRecK + q] = P.k0 + P.k2 * xq * xq;
   } else {
-    // J^{-1} from the FP64 cofactors and determinant, rounded once each
+    // J^{-1} from the FP64 cofactors and determinant, rounded once each;
+    // w det J follows in FP32 from the rounded determinant
     float* rec = static_cast<float*>(recp);
     float Cf[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Cf[i][j] = (float)C[i][j];
-    const float wdf = (float)wd;
-    const float sc = sqrtf(wdf) * (float)s / (float)det;
+      for (int j = 0; j < 3; ++j) Cf[i][j] = f64_to_f32_rn(C[i][j]);
+    const float detf = f64_to_f32_rn(det);
+    const float wdf = rr.wf[q] * detf * (float)(1.0 / (s * s * s));
+    const float sc = sqrtf(wdf) * (float)s / detf;
 #pragma unroll
     for (int a = 0; a < NN; ++a)
 #pragma unroll
@@ -180,8 +182,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
       const int a = hex8_corner_node(p);
       double v[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) v[i] = valid ? sX[le][a][i] - sX[le][0][i] : 0.0;
-      const double x0 = valid ? sX[le][0][0] : 0.0;
+      for (int i = 0; i < 3; ++i) v[i] = valid ? sX[le][a][i] : 0.0;
       hex8_modal(v);
       __syncwarp();
 #pragma unroll
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
           double acc = 0.0;
 #pragma unroll
           for (int k = 0; k < 8; ++k) acc = fma(sX[le][k][0], m[k], acc);
-          xq = x0 + 0.125 * acc;
+          xq = 0.125 * acc;
         }
         geo_finish<NN, PREC>(rr, P, q, id, J, 8.0, xq, rec);
       }

@@ -263,7 +263,7 @@ __device__ __forceinline__ void j2_tile_body(typename J2Cfg<TYPE, SLOT, PREC, SP
       const int a = hex8_corner_node(p);
       double v[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] - sm.X[le][0][i] : 0.0;
+      for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] : 0.0;
       hex8_modal(v);
       __syncwarp();
 #pragma unroll
@@ -431,7 +431,8 @@ __device__ __forceinline__ void persist_j2_item(unsigned char* raw, const J2Para
     j2_tile_body<TYPE, SLOT, PREC, SPLIT, FEA_SCATTER_ATOMIC>(sm, c_rules_j2[SLOT], P, e0, end);
 }
 
-template <int PREC>
+// ONLY == kRuleHex8: a mesh of hexes only (one tile body); -1: any type
+template <int PREC, int ONLY>
 __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ PersistJ2Args A) {
   constexpr int S2 = PersistJ2Cfg<PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_j2_smem[];
@@ -443,13 +444,19 @@ __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ P
     if (item < 0) break;
     const uint64_t t0 = global_ns();
     const WorkItem it = A.S.items[item];
-    const J2Params& P = A.table[it.entry];
     const int64_t first = it.first, end = (int64_t)it.first + it.count;
-    switch (A.slot[it.entry]) {
-      case kRulePyr8: persist_j2_item<FEA_PYR5, kRulePyr8, PREC, 1>(persist_j2_smem, P, first, end); break;
-      case kRulePrism6: persist_j2_item<FEA_PRISM6, kRulePrism6, PREC, S2>(persist_j2_smem, P, first, end); break;
-      case kRuleHex8: persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, P, first, end); break;
-      default: persist_j2_item<FEA_TET4, kRuleTet4, PREC, 1>(persist_j2_smem, P, first, end); break;
+    // entry t is type t: the parameters are read at constant offsets
+    if constexpr (ONLY == kRuleHex8) {
+      persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, A.table[FEA_HEX8], first, end);
+    } else {
+      switch (A.slot[it.entry]) {
+        case kRulePyr8: persist_j2_item<FEA_PYR5, kRulePyr8, PREC, 1>(persist_j2_smem, A.table[FEA_PYR5], first, end); break;
+        case kRulePrism6:
+          persist_j2_item<FEA_PRISM6, kRulePrism6, PREC, S2>(persist_j2_smem, A.table[FEA_PRISM6], first, end);
+          break;
+        case kRuleHex8: persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, A.table[FEA_HEX8], first, end); break;
+        default: persist_j2_item<FEA_TET4, kRuleTet4, PREC, 1>(persist_j2_smem, A.table[FEA_TET4], first, end); break;
+      }
     }
     sched_record(A.S, item, it.entry, t0);
   }
@@ -500,10 +507,12 @@ static J2Params j2_base_params(const fea_operator* op, fea_mesh* m, const int64_
   return P;
 }
 
-template <int PREC>
+template <int PREC, int ONLY>
 static int launch_persistent_j2_t(const PersistJ2Args& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
-  constexpr size_t smem = PersistJ2Cfg<PREC>::smem;
-  auto kern = k_persistent_j2<PREC>;
+  constexpr size_t smem = ONLY == kRuleHex8
+                              ? sizeof(typename J2Cfg<FEA_HEX8, kRuleHex8, PREC, PersistJ2Cfg<PREC>::S2>::Smem)
+                              : PersistJ2Cfg<PREC>::smem;
+  auto kern = k_persistent_j2<PREC, ONLY>;
   if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = n_ctas;
   if (grid <= 0) {
@@ -542,8 +551,14 @@ int launch_persistent_j2(const fea_operator* op, fea_mesh* m, const int64_t* row
     args.slot[t] = slots[t];
   }
   args.S = S;
-  return op->precision == FEA_FP64 ? launch_persistent_j2_t<FEA_FP64>(args, n_ctas, dry, s, grid_out)
-                                   : launch_persistent_j2_t<FEA_FP32_INTEGRATE>(args, n_ctas, dry, s, grid_out);
+  bool hex_only = m->group[FEA_HEX8].n > 0;
+  for (int t = 0; t < kNumTypes; ++t)
+    if (t != FEA_HEX8 && m->group[t].n) hex_only = false;
+  if (op->precision == FEA_FP64)
+    return hex_only ? launch_persistent_j2_t<FEA_FP64, kRuleHex8>(args, n_ctas, dry, s, grid_out)
+                    : launch_persistent_j2_t<FEA_FP64, -1>(args, n_ctas, dry, s, grid_out);
+  return hex_only ? launch_persistent_j2_t<FEA_FP32_INTEGRATE, kRuleHex8>(args, n_ctas, dry, s, grid_out)
+                  : launch_persistent_j2_t<FEA_FP32_INTEGRATE, -1>(args, n_ctas, dry, s, grid_out);
 }
 
 int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,

@@ -13,8 +13,11 @@ constexpr int kDefaultChunk = 128;
 void free_sched(fea_mesh* m) {
   cudaFree(m->items);
   cudaFree(m->sched_counter);
+  cudaFree(m->sched_heads);
   m->items = nullptr;
   m->sched_counter = nullptr;
+  m->sched_heads = nullptr;
+  m->sched_heads_n = 0;
   m->items_h.clear();
   m->items_chunk = 0;
 }
@@ -61,8 +64,9 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
   if (op->scatter != FEA_SCATTER_ATOMIC)
     return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: the persistent schedules use the ATOMIC scatter");
   if (op->chunk < 0 || op->chunk > (1 << 24)) return fail(FEA_ERR_ARG, "fea_assemble: chunk must be in [0, 2^24]");
-  if (op->schedule == FEA_SCHED_QUEUES && (!op->queue_d || !op->queue_off_d || op->n_ctas <= 0))
-    return fail(FEA_ERR_ARG, "fea_assemble: FEA_SCHED_QUEUES needs queue_d, queue_off_d and n_ctas > 0");
+  const bool queues = op->schedule == FEA_SCHED_QUEUES || op->schedule == FEA_SCHED_QUEUES_STEAL;
+  if (queues && (!op->queue_d || !op->queue_off_d || op->n_ctas <= 0))
+    return fail(FEA_ERR_ARG, "fea_assemble: the queue schedules need queue_d, queue_off_d and n_ctas > 0");
   if (op->n_ctas < 0) return fail(FEA_ERR_ARG, "fea_assemble: n_ctas must be >= 0");
   const int chunk = chunk_of(op);
   int rc = ensure_items(m, chunk, s);
@@ -74,6 +78,16 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
   FEA_CUDA(cudaMemsetAsync(A, 0, (size_t)D * D * m->nnz_node * sizeof(double), s));
   FEA_CUDA(cudaMemsetAsync(b, 0, (size_t)m->n_nodes * D * sizeof(double), s));
   FEA_CUDA(cudaMemsetAsync(m->sched_counter, 0, sizeof(int32_t), s));
+  if (op->schedule == FEA_SCHED_QUEUES_STEAL) {
+    if (m->sched_heads_n < op->n_ctas) {
+      cudaFree(m->sched_heads);
+      m->sched_heads = nullptr;
+      m->sched_heads_n = 0;
+      FEA_CUDA(cudaMalloc(&m->sched_heads, (size_t)op->n_ctas * sizeof(int32_t)));
+      m->sched_heads_n = op->n_ctas;
+    }
+    FEA_CUDA(cudaMemsetAsync(m->sched_heads, 0, (size_t)op->n_ctas * sizeof(int32_t), s));
+  }
   if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
   SchedArgs S;
   std::memset(&S, 0, sizeof(S));
@@ -85,6 +99,8 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
   S.queue_off = op->queue_off_d;
   S.item_ns = op->item_ns_d;
   S.item_cta = op->item_cta_d;
+  S.heads = m->sched_heads;
+  S.n_queues = op->n_ctas;
   if (S.n_items > 0) {
     rc = op->kind == FEA_OP_J2
              ? launch_persistent_j2(op, m, row_ptr, node_map, A, b, S, op->n_ctas, false, s, nullptr)

@@ -30,7 +30,7 @@ FEA_ERR_UNSUPPORTED = -8
 
 FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
 FEA_OP_DIFFUSION, FEA_OP_ELASTICITY, FEA_OP_J2 = 0, 1, 2
-FEA_SCHED_PER_TYPE, FEA_SCHED_STEAL, FEA_SCHED_QUEUES = 0, 1, 2
+FEA_SCHED_PER_TYPE, FEA_SCHED_STEAL, FEA_SCHED_QUEUES, FEA_SCHED_QUEUES_STEAL = 0, 1, 2, 3
 FEA_FP64, FEA_FP32_INTEGRATE, FEA_FP32_ADAPTIVE = 0, 1, 2
 FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS = 0, 1, 2, 3
 

@@ -120,10 +120,55 @@ def _time_assemble(s, op, reps=7):
     return float(np.median(ts))
 
 
-def test_mlp_packing_makespan_against_gauss_point_weights_and_stealing(capsys):
-    """The learned model packs the J2 work items at least as well as the
-    Gauss-point-weight heuristic (the paper's a-priori element weight);
-    dynamic work stealing is the reference makespan."""
+def _r2(pred_log_cost, y):
+    y = np.asarray(y, dtype=np.float64)
+    return 1.0 - np.var(y - pred_log_cost) / np.var(y)
+
+
+def _study(fea, s, base, chunk, Xkw, capsys, label):
+    """Stealing run (recording item timings), the model trained on them, and the
+    makespans of stealing and of LPT queues (+ stealing fallback) packed by the
+    model and by Gauss-point weights.  Returns the prediction R^2 of both cost
+    models (log ns per element) and the kernel times."""
+    import torch
+    types, _, counts = fea.fea_work_items(s.handle, chunk)
+    item_ns = torch.zeros(len(counts), dtype=torch.int64, device="cuda")
+    steal = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
+    res = {"steal": _time_assemble(s, steal)}
+    X = fea.fea_item_features(s.handle, chunk, len(counts), **Xkw)
+    y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device="cuda", dtype=torch.float32))
+    h = fea.fea_costmodel_create(6, M.xavier_init(6).astype(np.float32))
+    try:
+        fea.fea_costmodel_fit_scaler(h, X, y)
+        loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())
+        pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
+    finally:
+        fea.fea_costmodel_destroy(h)
+    yv = y.cpu().numpy().astype(np.float64)
+    # the Gauss-point model: log cost per element = log(n_q) + the best constant
+    gp_log = np.log(np.array([4, 8, 6, 8])[types].astype(np.float64))
+    gp_log = gp_log + (yv - gp_log).mean()
+    r2 = {"mlp": _r2(pred, yv), "gauss_points": _r2(gp_log, yv)}
+    grid = fea.fea_persistent_grid(steal, s.handle)
+    for name, cost in (("mlp", np.exp(pred) * counts),
+                       ("gauss_points", counts * np.array([4, 8, 6, 8])[types].astype(np.float64))):
+        q, off, _ = fea.fea_pack_lpt(cost, grid)
+        qd, od = torch.tensor(q, device="cuda"), torch.tensor(off, device="cuda")
+        for mode, suf in ((fea.FEA_SCHED_QUEUES, ""), (fea.FEA_SCHED_QUEUES_STEAL, "+steal")):
+            op = fea.make_operator(schedule=mode, n_ctas=grid, queue=qd, queue_off=od, chunk=chunk, **base)
+            res[name + suf] = _time_assemble(s, op)
+    with capsys.disabled():
+        print(f"\n{label} chunk {chunk}: {len(counts)} items on {grid} CTAs; loss {loss:.3f}; "
+              f"R^2 mlp {r2['mlp']:.3f} gauss-point {r2['gauss_points']:.3f}; ms: "
+              + ", ".join(f"{k} {v:.3f}" for k, v in res.items()))
+    return r2, res
+
+
+def test_cost_model_gain_on_elastoplastic_items(capsys):
+    """J2 work items cost more where Gauss points yield, which the Gauss-point
+    weights (uniform on a hex mesh) cannot see: the trained model explains the
+    measured item costs, and its packing is within noise of the heuristic's;
+    work stealing is the reference makespan."""
     import json
     import os
     import torch
@@ -135,36 +180,25 @@ def test_mlp_packing_makespan_against_gauss_point_weights_and_stealing(capsys):
         u = torch.tensor(U.reshape(-1), device="cuda")
         st1 = torch.empty((mesh.n_elems, 8, 7), dtype=torch.float64, device="cuda")
         s.assemble(fea.make_operator(kind=fea.FEA_OP_J2, precision=1, u=0.5 * u, state_out=st1))
-        chunk = 32
-        types, _, counts = fea.fea_work_items(s.handle, chunk)
-        n_items = len(counts)
-        item_ns = torch.zeros(n_items, dtype=torch.int64, device="cuda")
-        base = dict(kind=fea.FEA_OP_J2, precision=1, u=u, state_in=st1, chunk=chunk)
-        steal = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, item_ns=item_ns, **base)
-        t_steal = _time_assemble(s, steal)
-        # training data: the per-item timings the assembly recorded
-        X = fea.fea_item_features(s.handle, chunk, n_items, u, st1)
-        y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device="cuda", dtype=torch.float32))
-        h = fea.fea_costmodel_create(6, M.xavier_init(6).astype(np.float32))
-        try:
-            fea.fea_costmodel_fit_scaler(h, X, y)
-            loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())
-            pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
-        finally:
-            fea.fea_costmodel_destroy(h)
-        grid = fea.fea_persistent_grid(steal, s.handle)
-        cost_mlp = np.exp(pred) * counts
-        cost_gp = counts * np.array([4, 8, 6, 8])[types].astype(np.float64)
-        res = {}
-        for name, cost in (("mlp", cost_mlp), ("gauss_points", cost_gp)):
-            q, off, _ = fea.fea_pack_lpt(cost, grid)
-            qd, od = torch.tensor(q, device="cuda"), torch.tensor(off, device="cuda")
-            op = fea.make_operator(schedule=fea.FEA_SCHED_QUEUES, n_ctas=grid, queue=qd, queue_off=od, **base)
-            res[name] = _time_assemble(s, op)
-        with capsys.disabled():
-            print(f"\nJ2 40^3 chunk {chunk}: {n_items} items on {grid} CTAs; train loss {loss:.3f}; "
-                  f"makespan ms: steal {t_steal:.3f}, mlp {res['mlp']:.3f}, gauss-point {res['gauss_points']:.3f}")
-        assert loss < 1.0
-        assert res["mlp"] <= 1.02 * res["gauss_points"]
+        r2, res = _study(fea, s, dict(kind=fea.FEA_OP_J2, precision=1, u=u, state_in=st1), 32,
+                         dict(u=u, state_in=st1), capsys, "J2 40^3")
+        assert r2["mlp"] > r2["gauss_points"] + 0.2
+        assert res["mlp+steal"] <= 1.05 * res["gauss_points+steal"]
+    finally:
+        s.close()
+
+
+def test_cost_model_gain_on_a_hybrid_mesh(capsys):
+    """On a mixed tet/pyramid/prism/hex mesh the Gauss-point weights (4/8/6/8)
+    misjudge the per-type costs (which grow with nodes^2 x points); the model
+    learns them from the recorded item timings."""
+    fea = engine()
+    mesh = mg.hybrid_cube(40, 3)
+    s = fea.System.from_mesh(mesh, 1)
+    try:
+        r2, res = _study(fea, s, dict(kind=0, precision=1, tet_rule=1, k0=1.0, k2=1.0, source=1.0), 64, {},
+                         capsys, "hybrid 40^3 diffusion")
+        assert r2["mlp"] > max(r2["gauss_points"], 0.0) + 0.1
+        assert res["mlp"] <= 1.05 * res["gauss_points"]
     finally:
         s.close()

@@ -31,7 +31,7 @@ def _queues(n_items, n_ctas, seed):
 
 
 @pytest.mark.parametrize("chunk", [1, 7, 0])
-@pytest.mark.parametrize("schedule", ["steal", "queues"])
+@pytest.mark.parametrize("schedule", ["steal", "queues", "queues_steal"])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", list(SCHED_CASES))
 def test_persistent_schedules_match_oracle(oracle, name, precision, schedule, chunk):
@@ -54,7 +54,8 @@ def test_persistent_schedules_match_oracle(oracle, name, precision, schedule, ch
         else:
             grid = 5
             q, qo = _queues(n_items, grid, 11)
-            op = fea.make_operator(schedule=fea.FEA_SCHED_QUEUES, n_ctas=grid, queue=q, queue_off=qo, **kw)
+            mode = fea.FEA_SCHED_QUEUES if schedule == "queues" else fea.FEA_SCHED_QUEUES_STEAL
+            op = fea.make_operator(schedule=mode, n_ctas=grid, queue=q, queue_off=qo, **kw)
         s.A.fill_(float("nan"))
         s.assemble(op)
         s.check()
