@@ -41,6 +41,12 @@ NOMINAL_FP32_TFLOPS = 80.5     # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, same GB300"
 
+# DRAM bytes (read + write) of one launch of a kernel at the 128^3 workload: an
+# ncu capture of the 64^3 case (same kernel and launch shape, inputs larger than
+# L2) scaled by the element count, which its traffic grows with.  Remove an
+# entry whenever its kernel changes.
+TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.969472e6 + 468.289792e6)}
+
 # the kernel each variant spends its step in
 DOMINANT_KERNEL = {"atomic": "k_assemble_tile", "color": "k_assemble_tile (one launch per color)",
                    "rows": "k_rows_assemble", "block": "k_rows_assemble (block-task plan)"}
@@ -324,7 +330,8 @@ def run_ours(args, rank, world, local_rank):
             else:
                 roof = {"bound": "hbm", "achieved": by / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                         "peak_source": peak_kind, "algorithmic_bytes": by}
-        roof.update(frac=roof["achieved"] / roof["peak"], traffic=None, kernel=k_name, kernel_ms=k_ms)
+        roof.update(frac=roof["achieved"] / roof["peak"], kernel=k_name, kernel_ms=k_ms,
+                    traffic=TRAFFIC_BYTES.get(k_name) if args.n == 128 else None)
         line = {
             "metric": METRIC,
             "value": whole_job_rate(E, world, r["ms_per_step"]),
@@ -394,15 +401,17 @@ def _time_calls(fn, steps, warmup=2):
     return float(statistics.median(ts))
 
 
-def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk):
+def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, grid_fn=None):
     """Persistent schedules of one workload: work stealing (whose per-item timings train the
     cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, and
     the same queues with stealing as the fallback once a CTA's own queue is empty."""
     import torch
     from oracle import mlp_oracle
+    run = run or s.assemble
+    grid_fn = grid_fn or fea.fea_persistent_grid
     item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
     steal = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
-    out = {"persistent_steal": _time_calls(lambda: s.assemble(steal), steps)}
+    out = {"persistent_steal": _time_calls(lambda: run(steal), steps)}
     s.check()
     y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
     h = fea.fea_costmodel_create(6, mlp_oracle.xavier_init(6).astype(np.float32))
@@ -412,7 +421,7 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk):
     pred = fea.fea_costmodel_predict(h, X).cpu().numpy().astype(np.float64)
     train_s = time.perf_counter() - t0
     fea.fea_costmodel_destroy(h)
-    grid = fea.fea_persistent_grid(steal, s.handle)
+    grid = grid_fn(steal, s.handle)
     costs = {"mlp": np.exp(pred) * counts,
              "gauss_points": counts * np.array([4, 8, 6, 8])[types].astype(np.float64)}
     for name, cost in costs.items():
@@ -420,7 +429,7 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk):
         qd, od = torch.tensor(q, device=dev), torch.tensor(off, device=dev)
         for mode, suffix in ((fea.FEA_SCHED_QUEUES, ""), (fea.FEA_SCHED_QUEUES_STEAL, "_steal")):
             op = fea.make_operator(schedule=mode, n_ctas=grid, queue=qd, queue_off=od, chunk=chunk, **base)
-            out[f"{name}_queues{suffix}"] = _time_calls(lambda: s.assemble(op), steps)
+            out[f"{name}_queues{suffix}"] = _time_calls(lambda: run(op), steps)
             s.check()
     return out, {"train_loss": loss, "train_s": train_s, "epochs": 600, "items": len(counts), "chunk": chunk,
                  "grid": grid,
@@ -479,9 +488,18 @@ def config_j2(dev, steps=5):
         X = fea.fea_item_features(s.handle, chunk, len(counts), u, st1, device=dev)
         sched, mlp = schedule_study(fea, s, dict(precision=1, **base), counts, types, X, dev, steps, chunk)
         out.update({"fp32_" + k: v for k, v in sched.items()})
+        # the element-wise loop (no scatter): the Gauss-point update alone
+        sig = torch.empty((mesh.n_elems, 8, 6), dtype=torch.float64, device=dev)
+        loop = {"per_type": _time_calls(lambda: fea.fea_element_loop(fea.make_operator(**base), s.handle, sig), steps)}
+        lsched, lmlp = schedule_study(fea, s, base, counts, types, X, dev, steps, chunk,
+                                      run=lambda op: fea.fea_element_loop(op, s.handle, sig),
+                                      grid_fn=fea.fea_element_loop_grid)
+        loop.update(lsched)
         return {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
                             f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
-                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp}
+                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
+                "element_loop": {"ms": loop, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in loop.items()},
+                                 "mlp": lmlp}}
     finally:
         s.close()
 

@@ -277,6 +277,21 @@ int fea_work_items(const fea_mesh* mesh, int chunk, int64_t* n_items, int32_t* t
  * how many queues a FEA_SCHED_QUEUES packing should fill.  Host call. */
 int fea_persistent_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
 
+/* The element-wise loop without a scatter (the paper's second measured loop:
+ * the subgrid-scale update of Sec. 2.1.3, timed in Sec. 5.3, is a loop over
+ * the elements that updates per-element quantities and assembles nothing).  For op->kind == FEA_OP_J2 it runs the Gauss-point
+ * update of every element -- strain, radial return from state_in_d -- and
+ * writes state_out_d, yield_out_d, iters_out_d (fea_operator layout) and
+ * stress_d (float64 [n_elems][8][6], Cauchy stress tensor components xx, yy,
+ * zz, xy, yz, xz per point slot; may be NULL).  The mesh needs no pattern.
+ * op->schedule selects per-type launches or a persistent schedule (items,
+ * queues and item timings as for fea_assemble).  Stream-ordered; a failed
+ * return map latches FEA_ERR_NO_CONVERGENCE. */
+int fea_element_loop(const fea_operator* op, fea_mesh* mesh, double* stress_d, void* stream);
+
+/* Grid size of the persistent element loop (as fea_persistent_grid). */
+int fea_element_loop_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
+
 /* ---------------------------------------------------------------------------
  * Learned cost model (the GPU counterpart of the paper's dynamic load
  * balancing, Sec. 4: element costs are not known a priori).  A small MLP,

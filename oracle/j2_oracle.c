@@ -305,15 +305,16 @@ int64_t oracle_j2_assemble(int64_t n_nodes, int64_t n_elems, const uint8_t* type
 }
 
 /* ---------------------------------------------------------------------------
- * Gauss-point sweep without assembly (for the load-amplitude fixture): the
- * return map of every point of every element at displacement scale*U, from
- * state_n (NULL = virgin), writing the new state (may be NULL) and
- * returning the number of points that yielded, or -1 on an inverted element
- * or a failed return map.
+ * Gauss-point sweep without assembly (the element-wise loop; also the
+ * load-amplitude fixture): the return map of every point of every element at
+ * displacement scale*U, from state_n (NULL = virgin), writing the new state,
+ * the stress [E][8][6], the Newton iteration counts and the yield flags
+ * [E][8] (each may be NULL) and returning the number of points that yielded,
+ * or -1 on an inverted element or a failed return map.
  * ------------------------------------------------------------------------- */
 int64_t oracle_j2_sweep(int64_t n_elems, const uint8_t* types, const int64_t* conn_off, const int32_t* conn,
                         const double* coords, const double* prm, const double* U, double scale,
-                        const double* state_n, double* state) {
+                        const double* state_n, double* state, double* stress, int32_t* iters, uint8_t* yielded) {
   int64_t count = 0;
   double X[3 * J2_MAXN], Ue[3 * J2_MAXN];
   for (int64_t e = 0; e < n_elems; ++e) {
@@ -367,6 +368,10 @@ int64_t oracle_j2_sweep(int64_t n_elems, const uint8_t* types, const int64_t* co
         for (int i = 0; i < 6; ++i) state[56 * e + 7 * q + i] = ep[i];
         state[56 * e + 7 * q + 6] = al;
       }
+      if (stress)
+        for (int i = 0; i < 6; ++i) stress[48 * e + 6 * q + i] = sig[i];
+      if (iters) iters[8 * e + q] = it;
+      if (yielded) yielded[8 * e + q] = (uint8_t)yl;
       count += yl;
     }
   }

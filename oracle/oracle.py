@@ -79,7 +79,7 @@ def _extra_signatures():
         "oracle_j2_point": (_i32, [_p, _p, _p, ctypes.c_double, _p, _p, _p, _p, _p, _p]),
         "oracle_j2_element": (_i32, [_i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
         "oracle_j2_assemble": (_i64, [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
-        "oracle_j2_sweep": (_i64, [_i64, _p, _p, _p, _p, _p, _p, ctypes.c_double, _p, _p]),
+        "oracle_j2_sweep": (_i64, [_i64, _p, _p, _p, _p, _p, _p, ctypes.c_double, _p, _p, _p, _p, _p]),
     }
 
 
@@ -321,7 +321,24 @@ def j2_sweep(mesh, U, scale=1.0, state_n=None, want_state=False, **kw):
     st = np.zeros((mesh.n_elems, 8, 7)) if want_state else None
     sn = None if state_n is None else _c(state_n, np.float64)
     n = lib().oracle_j2_sweep(mesh.n_elems, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords), _ptr(prm), _ptr(U),
-                              float(scale), _ptr(sn), _ptr(st))
+                              float(scale), _ptr(sn), _ptr(st), None, None, None)
     if n < 0:
         raise NoConvergence("inverted element or failed return map")
     return (int(n), st) if want_state else int(n)
+
+
+def j2_points(mesh, U, state_n=None, **kw):
+    """The element-wise loop: per (element, point slot) the new state [E,8,7], stress [E,8,6],
+    Newton iteration counts and yield flags [E,8] (slots past the rule's points stay 0)."""
+    prm = j2_params(**kw)
+    E = mesh.n_elems
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64); U = _c(U, np.float64)
+    st = np.zeros((E, 8, 7)); sig = np.zeros((E, 8, 6))
+    it = np.zeros((E, 8), dtype=np.int32); yl = np.zeros((E, 8), dtype=np.uint8)
+    sn = None if state_n is None else _c(state_n, np.float64)
+    n = lib().oracle_j2_sweep(E, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords), _ptr(prm), _ptr(U), 1.0, _ptr(sn),
+                              _ptr(st), _ptr(sig), _ptr(it), _ptr(yl))
+    if n < 0:
+        raise NoConvergence("inverted element or failed return map")
+    return dict(state=st, stress=sig, iters=it, yielded=yl, n_yielded=int(n))

@@ -125,7 +125,9 @@ int launch_persistent_assemble(const fea_operator* op, fea_mesh* m, const int64_
                                int* grid_out);
 int launch_persistent_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
                          double* A, double* b, const SchedArgs& S, int n_ctas, bool dry, cudaStream_t s,
-                         int* grid_out);
+                         int* grid_out, double* stress = nullptr, bool points_only = false);
+int element_loop_persistent(const fea_operator* op, fea_mesh* m, double* stress, cudaStream_t s);
+int element_loop_j2(const fea_operator* op, fea_mesh* m, double* stress, cudaStream_t s);
 int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
                         double* A, double* b, cudaStream_t s);
 int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,

@@ -46,6 +46,7 @@ struct J2Params {
   double* state_out;
   uint8_t* yield_out;
   uint8_t* iters_out;
+  double* stress_out;     // element loop: [E][8][6] Cauchy stress per point slot (may be nullptr)
   double lam, mu, kappa;
   double s0, sinf, delta, hard, tol_g, tol_step;
   int max_iter;
@@ -210,6 +211,10 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
   }
   if (P.yield_out) P.yield_out[slot] = (uint8_t)r.yielded;
   if (P.iters_out) P.iters_out[slot] = (uint8_t)r.iters;
+  if (P.stress_out) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) P.stress_out[slot * 6 + i] = r.sig[i];
+  }
   const double W = rr.w[q] * det * (1.0 / (s * s * s));
   sm.C[le][q][0] = (R)W;
   sm.C[le][q][1] = (R)(W * (P.kappa - 2.0 * P.mu * r.theta / 3.0));
@@ -233,7 +238,8 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
 
 // One tile of EPC elements from launch index e0 (elements at or past n_end
 // are skipped).  Every thread of the CTA calls it; it ends with a barrier.
-template <int TYPE, int SLOT, int PREC, int SPLIT, int SC>
+// SCATTER = false is the element-wise loop: the Gauss-point update only.
+template <int TYPE, int SLOT, int PREC, int SPLIT, int SC, bool SCATTER = true>
 __device__ __forceinline__ void j2_tile_body(typename J2Cfg<TYPE, SLOT, PREC, SPLIT>::Smem& sm, const RefRule& rr,
                                              const J2Params& P, int64_t e0, int64_t n_end) {
   using Cfg = J2Cfg<TYPE, SLOT, PREC, SPLIT>;
@@ -303,7 +309,7 @@ __device__ __forceinline__ void j2_tile_body(typename J2Cfg<TYPE, SLOT, PREC, SP
   const int lw = lane / LPE;
   const int le = warp * EPW + lw;
   const int64_t et = e0 + le;
-  if (lw < EPW && et < n_end) {
+  if (SCATTER && lw < EPW && et < n_end) {
     const int r = lane % LPE;
     const int a = r % NN, b0 = (r / NN) * NB;
     R K[NB][3][3], rhs[3] = {R(0), R(0), R(0)};
@@ -370,6 +376,26 @@ __global__ void __launch_bounds__(128) k_j2_tile(const __grid_constant__ RefRule
                                             (int64_t)blockIdx.x * Cfg::EPC, P.n);
 }
 
+// element-wise loop: one tile of Gauss-point updates per CTA
+template <int TYPE, int SLOT>
+__global__ void __launch_bounds__(128) k_j2_points(const __grid_constant__ RefRule rr, const __grid_constant__ J2Params P) {
+  using Cfg = J2Cfg<TYPE, SLOT, FEA_FP32_INTEGRATE, 1>;
+  extern __shared__ __align__(16) unsigned char j2_smem_raw[];
+  j2_tile_body<TYPE, SLOT, FEA_FP32_INTEGRATE, 1, FEA_SCATTER_ATOMIC, false>(
+      *reinterpret_cast<typename Cfg::Smem*>(j2_smem_raw), rr, P, (int64_t)blockIdx.x * Cfg::EPC, P.n);
+}
+
+template <int TYPE, int SLOT>
+static int launch_j2_points(const J2Params& P, cudaStream_t s) {
+  using Cfg = J2Cfg<TYPE, SLOT, FEA_FP32_INTEGRATE, 1>;
+  constexpr size_t smem = sizeof(typename Cfg::Smem);
+  auto kern = k_j2_points<TYPE, SLOT>;
+  if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid_for(P.n, Cfg::EPC), Cfg::THREADS, smem, s>>>(host_rule(SLOT), P);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
 template <int TYPE, int SLOT, int PREC, int SPLIT, int SC>
 static int launch_j2(const J2Params& P, cudaStream_t s) {
   using Cfg = J2Cfg<TYPE, SLOT, PREC, SPLIT>;
@@ -423,16 +449,16 @@ struct PersistJ2Cfg {
                                     mx(bytes<FEA_PRISM6, kRulePrism6, S2>(), bytes<FEA_HEX8, kRuleHex8, S2>()));
 };
 
-template <int TYPE, int SLOT, int PREC, int SPLIT>
+template <int TYPE, int SLOT, int PREC, int SPLIT, bool SCATTER>
 __device__ __forceinline__ void persist_j2_item(unsigned char* raw, const J2Params& P, int64_t first, int64_t end) {
   using Cfg = J2Cfg<TYPE, SLOT, PREC, SPLIT>;
   auto& sm = *reinterpret_cast<typename Cfg::Smem*>(raw);
   for (int64_t e0 = first; e0 < end; e0 += Cfg::EPC)
-    j2_tile_body<TYPE, SLOT, PREC, SPLIT, FEA_SCATTER_ATOMIC>(sm, c_rules_j2[SLOT], P, e0, end);
+    j2_tile_body<TYPE, SLOT, PREC, SPLIT, FEA_SCATTER_ATOMIC, SCATTER>(sm, c_rules_j2[SLOT], P, e0, end);
 }
 
 // ONLY == kRuleHex8: a mesh of hexes only (one tile body); -1: any type
-template <int PREC, int ONLY>
+template <int PREC, int ONLY, bool SCATTER>
 __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ PersistJ2Args A) {
   constexpr int S2 = PersistJ2Cfg<PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_j2_smem[];
@@ -447,15 +473,15 @@ __global__ void __launch_bounds__(128) k_persistent_j2(const __grid_constant__ P
     const int64_t first = it.first, end = (int64_t)it.first + it.count;
     // entry t is type t: the parameters are read at constant offsets
     if constexpr (ONLY == kRuleHex8) {
-      persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, A.table[FEA_HEX8], first, end);
+      persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2, SCATTER>(persist_j2_smem, A.table[FEA_HEX8], first, end);
     } else {
       switch (A.slot[it.entry]) {
-        case kRulePyr8: persist_j2_item<FEA_PYR5, kRulePyr8, PREC, 1>(persist_j2_smem, A.table[FEA_PYR5], first, end); break;
+        case kRulePyr8: persist_j2_item<FEA_PYR5, kRulePyr8, PREC, 1, SCATTER>(persist_j2_smem, A.table[FEA_PYR5], first, end); break;
         case kRulePrism6:
-          persist_j2_item<FEA_PRISM6, kRulePrism6, PREC, S2>(persist_j2_smem, A.table[FEA_PRISM6], first, end);
+          persist_j2_item<FEA_PRISM6, kRulePrism6, PREC, S2, SCATTER>(persist_j2_smem, A.table[FEA_PRISM6], first, end);
           break;
-        case kRuleHex8: persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2>(persist_j2_smem, A.table[FEA_HEX8], first, end); break;
-        default: persist_j2_item<FEA_TET4, kRuleTet4, PREC, 1>(persist_j2_smem, A.table[FEA_TET4], first, end); break;
+        case kRuleHex8: persist_j2_item<FEA_HEX8, kRuleHex8, PREC, S2, SCATTER>(persist_j2_smem, A.table[FEA_HEX8], first, end); break;
+        default: persist_j2_item<FEA_TET4, kRuleTet4, PREC, 1, SCATTER>(persist_j2_smem, A.table[FEA_TET4], first, end); break;
       }
     }
     sched_record(A.S, item, it.entry, t0);
@@ -507,12 +533,12 @@ static J2Params j2_base_params(const fea_operator* op, fea_mesh* m, const int64_
   return P;
 }
 
-template <int PREC, int ONLY>
+template <int PREC, int ONLY, bool SCATTER = true>
 static int launch_persistent_j2_t(const PersistJ2Args& args, int n_ctas, bool dry, cudaStream_t s, int* grid_out) {
   constexpr size_t smem = ONLY == kRuleHex8
                               ? sizeof(typename J2Cfg<FEA_HEX8, kRuleHex8, PREC, PersistJ2Cfg<PREC>::S2>::Smem)
                               : PersistJ2Cfg<PREC>::smem;
-  auto kern = k_persistent_j2<PREC, ONLY>;
+  auto kern = k_persistent_j2<PREC, ONLY, SCATTER>;
   if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = n_ctas;
   if (grid <= 0) {
@@ -532,14 +558,15 @@ static int launch_persistent_j2_t(const PersistJ2Args& args, int n_ctas, bool dr
 
 int launch_persistent_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
                          double* A, double* b, const SchedArgs& S, int n_ctas, bool dry, cudaStream_t s,
-                         int* grid_out) {
+                         int* grid_out, double* stress, bool points_only) {
   if (!dry) {
     int rc = j2_validate(op);
     if (rc) return rc;
   }
   PersistJ2Args args;
   std::memset(&args, 0, sizeof(args));
-  const J2Params base = j2_base_params(op, m, row_ptr, node_map, A, b);
+  J2Params base = j2_base_params(op, m, row_ptr, node_map, A, b);
+  base.stress_out = stress;
   const int slots[kNumTypes] = {kRuleTet4, kRulePyr8, kRulePrism6, kRuleHex8};
   for (int t = 0; t < kNumTypes; ++t) {
     args.table[t] = base;
@@ -554,6 +581,9 @@ int launch_persistent_j2(const fea_operator* op, fea_mesh* m, const int64_t* row
   bool hex_only = m->group[FEA_HEX8].n > 0;
   for (int t = 0; t < kNumTypes; ++t)
     if (t != FEA_HEX8 && m->group[t].n) hex_only = false;
+  if (points_only)  // the element-wise loop: Gauss-point updates only
+    return hex_only ? launch_persistent_j2_t<FEA_FP32_INTEGRATE, kRuleHex8, false>(args, n_ctas, dry, s, grid_out)
+                    : launch_persistent_j2_t<FEA_FP32_INTEGRATE, -1, false>(args, n_ctas, dry, s, grid_out);
   if (op->precision == FEA_FP64)
     return hex_only ? launch_persistent_j2_t<FEA_FP64, kRuleHex8>(args, n_ctas, dry, s, grid_out)
                     : launch_persistent_j2_t<FEA_FP64, -1>(args, n_ctas, dry, s, grid_out);
@@ -620,4 +650,48 @@ int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, con
   return FEA_OK;
 }
 
+// The element-wise loop (no scatter): the J2 update at every Gauss point,
+// per type or by a persistent schedule (sched.cuh), writing the new state,
+// the stress, the yield flags and the Newton iteration counts.
+int element_loop_j2(const fea_operator* op, fea_mesh* m, double* stress, cudaStream_t s) {
+  int rc = j2_validate(op);
+  if (rc) return rc;
+  if (op->schedule != FEA_SCHED_PER_TYPE) return element_loop_persistent(op, m, stress, s);
+  cudaEvent_t* ev = (cudaEvent_t*)op->events;
+  const int nev = ev ? op->n_events : 0;
+  if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+  if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+  J2Params P = j2_base_params(op, m, nullptr, nullptr, nullptr, nullptr);
+  P.stress_out = stress;
+  int launched = 0;
+  for (int t = 0; t < kNumTypes; ++t) {
+    const TypeGroup& g = m->group[t];
+    if (!g.n) continue;
+    P.tconn = g.conn;
+    P.ids = g.ids;
+    P.mapoff = g.mapoff;
+    P.list = nullptr;
+    P.n = g.n;
+    switch (t) {
+      case FEA_TET4: rc = launch_j2_points<FEA_TET4, kRuleTet4>(P, s); break;
+      case FEA_PYR5: rc = launch_j2_points<FEA_PYR5, kRulePyr8>(P, s); break;
+      case FEA_PRISM6: rc = launch_j2_points<FEA_PRISM6, kRulePrism6>(P, s); break;
+      default: rc = launch_j2_points<FEA_HEX8, kRuleHex8>(P, s); break;
+    }
+    if (rc) return rc;
+    if (2 + launched < nev) FEA_CUDA(cudaEventRecord(ev[2 + launched], s));
+    ++launched;
+  }
+  return FEA_OK;
+}
+
 }  // namespace fea
+
+extern "C" int fea_element_loop(const fea_operator* op, fea_mesh* mesh, double* stress_d, void* stream) {
+  using namespace fea;
+  if (!op || !mesh) return fail(FEA_ERR_ARG, "fea_element_loop: null argument");
+  if (op->kind != FEA_OP_J2) return fail(FEA_ERR_UNSUPPORTED, "fea_element_loop: the loop runs the J2 operator");
+  if (op->schedule < FEA_SCHED_PER_TYPE || op->schedule > FEA_SCHED_QUEUES_STEAL)
+    return fail(FEA_ERR_ARG, "fea_element_loop: unknown schedule");
+  return element_loop_j2(op, mesh, stress_d, (cudaStream_t)stream);
+}

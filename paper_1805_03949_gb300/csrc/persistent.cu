@@ -59,24 +59,16 @@ static int ensure_items(fea_mesh* m, int chunk, cudaStream_t s) {
 
 static int chunk_of(const fea_operator* op) { return op->chunk > 0 ? op->chunk : kDefaultChunk; }
 
-int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
-                        double* A, double* b, cudaStream_t s) {
-  if (op->scatter != FEA_SCATTER_ATOMIC)
-    return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: the persistent schedules use the ATOMIC scatter");
+// scheduler state of one persistent launch: items of the operator's chunk,
+// the stealing counter and the queue heads, reset on the stream
+static int prepare_sched(const fea_operator* op, fea_mesh* m, cudaStream_t s, SchedArgs* S) {
   if (op->chunk < 0 || op->chunk > (1 << 24)) return fail(FEA_ERR_ARG, "fea_assemble: chunk must be in [0, 2^24]");
   const bool queues = op->schedule == FEA_SCHED_QUEUES || op->schedule == FEA_SCHED_QUEUES_STEAL;
   if (queues && (!op->queue_d || !op->queue_off_d || op->n_ctas <= 0))
     return fail(FEA_ERR_ARG, "fea_assemble: the queue schedules need queue_d, queue_off_d and n_ctas > 0");
   if (op->n_ctas < 0) return fail(FEA_ERR_ARG, "fea_assemble: n_ctas must be >= 0");
-  const int chunk = chunk_of(op);
-  int rc = ensure_items(m, chunk, s);
+  int rc = ensure_items(m, chunk_of(op), s);
   if (rc) return rc;
-  const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
-  cudaEvent_t* ev = (cudaEvent_t*)op->events;
-  const int nev = ev ? op->n_events : 0;
-  if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
-  FEA_CUDA(cudaMemsetAsync(A, 0, (size_t)D * D * m->nnz_node * sizeof(double), s));
-  FEA_CUDA(cudaMemsetAsync(b, 0, (size_t)m->n_nodes * D * sizeof(double), s));
   FEA_CUDA(cudaMemsetAsync(m->sched_counter, 0, sizeof(int32_t), s));
   if (op->schedule == FEA_SCHED_QUEUES_STEAL) {
     if (m->sched_heads_n < op->n_ctas) {
@@ -88,23 +80,55 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
     }
     FEA_CUDA(cudaMemsetAsync(m->sched_heads, 0, (size_t)op->n_ctas * sizeof(int32_t), s));
   }
-  if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+  std::memset(S, 0, sizeof(*S));
+  S->items = m->items;
+  S->n_items = (int32_t)m->items_h.size();
+  S->mode = op->schedule;
+  S->counter = m->sched_counter;
+  S->queue = op->queue_d;
+  S->queue_off = op->queue_off_d;
+  S->item_ns = op->item_ns_d;
+  S->item_cta = op->item_cta_d;
+  S->heads = m->sched_heads;
+  S->n_queues = op->n_ctas;
+  return FEA_OK;
+}
+
+int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
+                        double* A, double* b, cudaStream_t s) {
+  if (op->scatter != FEA_SCATTER_ATOMIC)
+    return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: the persistent schedules use the ATOMIC scatter");
+  const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
+  cudaEvent_t* ev = (cudaEvent_t*)op->events;
+  const int nev = ev ? op->n_events : 0;
+  if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+  FEA_CUDA(cudaMemsetAsync(A, 0, (size_t)D * D * m->nnz_node * sizeof(double), s));
+  FEA_CUDA(cudaMemsetAsync(b, 0, (size_t)m->n_nodes * D * sizeof(double), s));
   SchedArgs S;
-  std::memset(&S, 0, sizeof(S));
-  S.items = m->items;
-  S.n_items = (int32_t)m->items_h.size();
-  S.mode = op->schedule;
-  S.counter = m->sched_counter;
-  S.queue = op->queue_d;
-  S.queue_off = op->queue_off_d;
-  S.item_ns = op->item_ns_d;
-  S.item_cta = op->item_cta_d;
-  S.heads = m->sched_heads;
-  S.n_queues = op->n_ctas;
+  int rc = prepare_sched(op, m, s, &S);
+  if (rc) return rc;
+  if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
   if (S.n_items > 0) {
     rc = op->kind == FEA_OP_J2
              ? launch_persistent_j2(op, m, row_ptr, node_map, A, b, S, op->n_ctas, false, s, nullptr)
              : launch_persistent_assemble(op, m, row_ptr, node_map, A, b, S, op->n_ctas, false, s, nullptr);
+    if (rc) return rc;
+  }
+  if (nev > 2) FEA_CUDA(cudaEventRecord(ev[2], s));
+  return FEA_OK;
+}
+
+int element_loop_persistent(const fea_operator* op, fea_mesh* m, double* stress, cudaStream_t s) {
+  cudaEvent_t* ev = (cudaEvent_t*)op->events;
+  const int nev = ev ? op->n_events : 0;
+  if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+  SchedArgs S;
+  int rc = prepare_sched(op, m, s, &S);
+  if (rc) return rc;
+  if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+  if (S.n_items > 0) {
+    rc = launch_persistent_j2(op, m, nullptr, nullptr, nullptr, nullptr, S, op->n_ctas, false, s, nullptr, stress,
+                              true);
     if (rc) return rc;
   }
   if (nev > 2) FEA_CUDA(cudaEventRecord(ev[2], s));
@@ -140,6 +164,14 @@ int fea_persistent_grid(const fea_operator* op, fea_mesh* m, int* n_ctas) {
              ? launch_persistent_j2(op, m, nullptr, nullptr, nullptr, nullptr, S, op->n_ctas, true, nullptr, n_ctas)
              : launch_persistent_assemble(op, m, nullptr, nullptr, nullptr, nullptr, S, op->n_ctas, true, nullptr,
                                           n_ctas);
+}
+
+int fea_element_loop_grid(const fea_operator* op, fea_mesh* m, int* n_ctas) {
+  if (!op || !m || !n_ctas) return fail(FEA_ERR_ARG, "fea_element_loop_grid: null argument");
+  SchedArgs S;
+  std::memset(&S, 0, sizeof(S));
+  return launch_persistent_j2(op, m, nullptr, nullptr, nullptr, nullptr, S, op->n_ctas, true, nullptr, n_ctas, nullptr,
+                              true);
 }
 
 }  // extern "C"

@@ -26,9 +26,7 @@
 // -- nine FMAs per point for elasticity.
 //
 // In FEA_FP32_INTEGRATE mode each element's contribution is integrated in
-// FP32 and the contributions of an entry are summed as an unevaluated FP32
-// pair (error-free TwoSum), then rounded once to FP64 with integer
-// instructions; FEA_FP64 computes and sums in FP64.
+// FP32, widened exactly and summed in FP64; FEA_FP64 computes and sums in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

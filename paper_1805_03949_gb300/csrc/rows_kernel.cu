@@ -10,9 +10,9 @@
 //
 // Task (i, j): for each contributing element e (node i at local a, j at b)
 //   M_e = sum_q g^_a(q) (x) g^_b(q),   K_e = lam M_e + mu M_e^T + mu tr(M_e) I
-// (diffusion: K_e = sum_q k(x_q) g^_a . g^_b); the K_e are summed as an FP32
-// TwoSum pair (FP32_INTEGRATE) or in FP64, rounded once to FP64 and written to
-// row i -- and, transposed, to row j when j belongs to the same block.
+// (diffusion: K_e = sum_q k(x_q) g^_a . g^_b); the K_e are summed in FP64
+// (FP32_INTEGRATE: each FP32 K_e widened exactly) and written to row i --
+// and, transposed, to row j when j belongs to the same block.
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -89,7 +89,12 @@ __device__ __forceinline__ int rule_slot_of(int type, int tet_nq) {
                           : type == FEA_PYR5 ? kRulePyr8 : type == FEA_PRISM6 ? kRulePrism6 : kRuleHex8;
 }
 
-// accumulator of one entry: FP64 sums, or FP32 pairs (hi, lo)
+// accumulator of one entry: FP64 sums.  FP32-integrate contributions are
+// widened exactly (integer instructions) and added in FP64, so the entry is
+// the FP64 sum of the FP32 element contributions, rounded at every add like
+// the atomic scatter's.  (An error-free FP32 pair (TwoSum) with one final
+// rounding measured slower on GB300: its renormalisation and integer FP64
+// assembly per entry cost more than one FP64 add per contribution.)
 template <int PREC>
 struct Acc;
 template <>
@@ -101,10 +106,10 @@ struct Acc<FEA_FP64> {
 };
 template <>
 struct Acc<FEA_FP32_INTEGRATE> {
-  float hi = 0.0f, lo = 0.0f;
-  __device__ __forceinline__ void set(float x) { hi = x; lo = 0.0f; }
-  __device__ __forceinline__ void add(float x) { two_sum_acc(hi, lo, x); }
-  __device__ __forceinline__ double value() const { return ff_to_f64(hi, lo); }
+  double v = 0.0;
+  __device__ __forceinline__ void set(float x) { v = f32_to_f64_exact(x); }
+  __device__ __forceinline__ void add(float x) { v += f32_to_f64_exact(x); }
+  __device__ __forceinline__ double value() const { return v; }
 };
 
 // element data: staged in shared memory, or read through L1

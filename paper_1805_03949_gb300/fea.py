@@ -97,6 +97,8 @@ def _load():
         "fea_costmodel_predict": (I32, [P, P, I64, P, P]),
         "fea_item_features": (I32, [P, I32, P, P, P, P]),
         "fea_pack_lpt": (I32, [P, I64, I32, P, P, P]),
+        "fea_element_loop": (I32, [ctypes.POINTER(fea_operator), P, P, P]),
+        "fea_element_loop_grid": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_batch_create": (I32, [ctypes.POINTER(fea_operator), I32, P, ctypes.POINTER(P)]),
         "fea_batch_destroy": (I32, [P]),
         "fea_batch_set_config": (I32, [P, I32, I32]),
@@ -385,6 +387,16 @@ class Batch:
         if self.handle:
             _check(_lib.fea_batch_destroy(self.handle))
             self.handle = None
+
+
+def fea_element_loop(op: "fea_operator", h, stress=None, stream=None):
+    _check(_lib.fea_element_loop(ctypes.byref(op), h, _dptr(stress), _stream(stream)))
+
+
+def fea_element_loop_grid(op: "fea_operator", h) -> int:
+    n = ctypes.c_int32()
+    _check(_lib.fea_element_loop_grid(ctypes.byref(op), h, ctypes.byref(n)))
+    return int(n.value)
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:

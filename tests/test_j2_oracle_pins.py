@@ -215,3 +215,30 @@ def test_global_assembly_invariants(oracle):
     assert n1 == int(r1["yielded"].sum())
     np.testing.assert_array_equal(st1, r1["state"])
     assert oracle.j2_sweep(mesh, U, 1.0, st1) == int(r2["yielded"].sum())
+
+
+def test_point_loop_agrees_with_the_assembly_and_its_stress_gives_f_int(oracle):
+    """The element-wise loop's state, flags and counts equal the assembly's; its
+    stresses, pushed through B^T by numpy, rebuild the internal force vector."""
+    mesh = mg.hex_cube(3, 0.2, 4)
+    U = mg.fourier_displacement(mesh.coords, 1.5e-4, seed=4)
+    r1 = oracle.j2_assemble(mesh, 0.5 * U)
+    r2 = oracle.j2_assemble(mesh, U, r1["state"])
+    pts = oracle.j2_points(mesh, U, r1["state"])
+    np.testing.assert_array_equal(pts["state"], r2["state"])
+    np.testing.assert_array_equal(pts["iters"], r2["iters"])
+    np.testing.assert_array_equal(pts["yielded"], r2["yielded"])
+    assert 0 < pts["n_yielded"] < 8 * mesh.n_elems
+    q, w = oracle.quadrature(mg.HEX8)
+    f = np.zeros((mesh.n_nodes, 3))
+    for e in range(mesh.n_elems):
+        nodes = mesh.element_nodes(e)
+        X = mesh.coords[nodes]
+        for k in range(8):
+            _, dN = oracle.shape(mg.HEX8, q[k])
+            J = X.T @ dN
+            G = dN @ np.linalg.inv(J)
+            s = pts["stress"][e, k]
+            S = np.array([[s[0], s[3], s[5]], [s[3], s[1], s[4]], [s[5], s[4], s[2]]])
+            f[nodes] += w[k] * np.linalg.det(J) * G @ S
+    np.testing.assert_allclose(f.reshape(-1), r2["b"], rtol=0, atol=1e-12 * np.abs(r2["b"]).max())
