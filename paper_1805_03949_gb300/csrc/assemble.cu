@@ -831,7 +831,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     int rc = geometry_pass(op, m, s, &records, &geo);
     if (rc) return rc;
     for (int k = 2; k < 2 + geo && k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
-    rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s);
+    rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s, nullptr);
     if (rc) return rc;
     for (int k = 2 + geo; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     return FEA_OK;
@@ -850,14 +850,17 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
   if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
   if (op->scatter == FEA_SCATTER_BLOCK) {
-    // geometry records, then one CTA per element block: interior entries are
+    // geometry records (computed by the task kernel itself for hex meshes in
+    // FP32-integrate), then one CTA per element block: interior entries are
     // stored, block-boundary entries added atomically into the zeroed A and b
     void* records = nullptr;
     int geo = 0;
-    int rc = geometry_pass(op, m, s, &records, &geo);
-    if (rc) return rc;
+    if (!fused_geometry(op, *bplan)) {
+      int rc = geometry_pass(op, m, s, &records, &geo);
+      if (rc) return rc;
+    }
     for (int k = 2; k < 2 + geo && k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
-    rc = launch_task_kernel(op, *bplan, records, row_ptr, A, b, m->status, s);
+    int rc = launch_task_kernel(op, *bplan, records, row_ptr, A, b, m->status, s, m);
     if (rc) return rc;
     for (int k = 2 + geo; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     return FEA_OK;
@@ -934,7 +937,11 @@ int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
     return FEA_OK;
   }
   if (op->scatter == FEA_SCATTER_ROWS || op->scatter == FEA_SCATTER_BLOCK) {
-    *n = geometry_launches(m) + 1;  // geometry pass per element type, then the task kernel
+    // geometry pass per element type, then the task kernel (block-task plans
+    // of hex meshes in FP32-integrate compute the geometry in the task kernel)
+    const bool fused = op->scatter == FEA_SCATTER_BLOCK && op->precision == FEA_FP32_INTEGRATE &&
+                       m->group[FEA_HEX8].n == m->n_elems;
+    *n = fused ? 1 : geometry_launches(m) + 1;
     return FEA_OK;
   }
   if (op->scatter == FEA_SCATTER_COLOR) {

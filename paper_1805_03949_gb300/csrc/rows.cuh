@@ -97,7 +97,11 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
 // the block-task plan of a mesh, built on first use
 int ensure_blocks_plan(fea_mesh* m, int ndof, cudaStream_t s, RowsPlan** out);
 // launch the task kernel of a plan (ROWS or BLOCK) on precomputed geometry records
+// Block-task plans of hex meshes in FEA_FP32_INTEGRATE compute the geometry
+// records inside the task kernel (every element belongs to one block).
+bool fused_geometry(const fea_operator* op, const RowsPlan& RP);
+// mesh: non-null enables the fused geometry where fused_geometry() holds
 int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* records, const int64_t* row_ptr,
-                       double* A, double* b, DevStatus* st, cudaStream_t s);
+                       double* A, double* b, DevStatus* st, cudaStream_t s, const fea_mesh* mesh);
 
 }  // namespace fea

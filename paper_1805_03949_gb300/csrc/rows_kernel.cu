@@ -13,6 +13,7 @@
 // (diffusion: K_e = sum_q k(x_q) g^_a . g^_b); the K_e are summed in FP64
 // (FP32_INTEGRATE: each FP32 K_e widened exactly) and written to row i --
 // and, transposed, to row j when j belongs to the same block.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -43,6 +44,14 @@ struct RowsArgs {
   double lam, mu, src, f[3];
   float Ntab[kNumRules][8][8];    // N_a(q) per rule slot, for the right-hand side
   double Ntab64[kNumRules][8][8];
+  // fused geometry (block-task plan, hex8, FP32-integrate): the CTA computes
+  // the records of its own elements from the mesh instead of reading them
+  const double* coords;
+  const int64_t* conn_off;
+  const int32_t* conn;
+  double k0, k2;
+  int diffusion;
+  RefRule hex;
 };
 
 // --- TMA bulk copy global -> shared with an mbarrier (bounded wait) --------
@@ -51,6 +60,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -122,9 +139,198 @@ __device__ __forceinline__ R ld_rec(const R* p) {
 }
 
 // HEX: every element is a hex8 with 8 points (compile-time loop bounds).
-// STAGE: the halo elements' records are bulk-copied into shared memory (FP32).
+// FP32 record of point p (= the thread's lane in its group of 8) of hex
+// element id, from the FP64 modal Jacobian: every lane of the warp calls it.
+__device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, int64_t id, float* rec) {
+  const int p = threadIdx.x & 7;
+  double v[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    const int64_t node = P.conn[P.conn_off[id] + hex8_corner_node(p)];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = P.coords[3 * node + i];
+  }
+  hex8_modal(v);
+  double c[8][3];
+  const int base = threadIdx.x & 24;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[k][i] = __shfl_sync(0xffffffffu, v[i], base | k);
+  if (!valid) return;
+  double J[3][3];
+  hex8_jacobian(c, p, J);
+  double C[3][3];
+  cofactors(J, C);
+  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  if (!(det > 0.0)) {
+    latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)id);
+    return;
+  }
+  // J' = 8 J: det J = det'/512, J^{-T} = 8 C'/det'
+  float Cf[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Cf[i][j] = f64_to_f32_rn(C[i][j]);
+  const float detf = f64_to_f32_rn(det);
+  const float wdf = P.hex.wf[p] * detf * (1.0f / 512.0f);
+  const float sc = sqrtf(wdf) * 8.0f / detf;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      rec[p * 24 + 3 * a + i] =
+          (P.hex.dNf[p][a][0] * Cf[i][0] + P.hex.dNf[p][a][1] * Cf[i][1] + P.hex.dNf[p][a][2] * Cf[i][2]) * sc;
+  rec[kRecW + p] = wdf;
+  if (P.diffusion) {
+    const double g = 0.57735026918962576451;
+    const double xs = (p & 1) ? g : -g, ys = (p & 2) ? g : -g, zs = (p & 4) ? g : -g;
+    const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fma(c[k][0], m[k], acc);
+    const float x = (float)(0.125 * acc);
+    rec[kRecK + p] = (float)P.k0 + (float)P.k2 * x * x;
+  }
+}
+
+// The entry-block tasks of one block, by threads tid, tid + nthreads, ...
+// (records staged in shared memory when STAGE, else read from `rec`).
 template <int OP, int PREC, bool HEX, bool STAGE>
+__device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
+                                          const typename std::conditional<PREC == FEA_FP64, double, float>::type* s_recs,
+                                          const int64_t* s_rs, const RowTask* s_tasks, const uint16_t* s_contrib,
+                                          const int32_t* s_hid, const int32_t* lnodes, int tid, int nthreads) {
+  using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
+  constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
+  const R* rec = reinterpret_cast<const R*>(P.rec);
+  const R lam = (R)P.lam, mu = (R)P.mu;
+  for (int t = tid; t < H.n_tasks; t += nthreads) {
+    const RowTask T = s_tasks[t];
+    const bool diag = T.flags & kTaskDiag;
+    Acc<PREC> acc[D][D];
+    Acc<PREC> bacc[D];
+#pragma unroll 1
+    for (int c = 0; c < T.nc; ++c) {
+      const int code = s_contrib[T.coff + c];
+      const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
+      const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
+      const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
+      const R* re = STAGE ? s_recs + (size_t)h * kRowsRecSmem : rec + (int64_t)s_hid[h] * kRecStride;
+      const R* ga = re + 3 * a;
+      const R* gb = re + 3 * bn;
+      R K[D][D];
+      if constexpr (OP == FEA_OP_DIFFUSION) {
+        R s = R(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (!HEX && q >= nq) break;
+          const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
+                  x2 = ld_rec<STAGE>(ga + 24 * q + 2);
+          const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
+                  y2 = ld_rec<STAGE>(gb + 24 * q + 2);
+          s += ld_rec<STAGE>(re + kRecK + q) * (x0 * y0 + x1 * y1 + x2 * y2);
+        }
+        K[0][0] = s;
+      } else {
+        R M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (!HEX && q >= nq) break;
+          const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
+                  x2 = ld_rec<STAGE>(ga + 24 * q + 2);
+          const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
+                  y2 = ld_rec<STAGE>(gb + 24 * q + 2);
+          M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
+          M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
+          M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
+        }
+        const R tr = mu * (M[0][0] + M[1][1] + M[2][2]);
+#pragma unroll
+        for (int c1 = 0; c1 < 3; ++c1)
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) K[c1][c2] = lam * M[c1][c2] + mu * M[c2][c1] + (c1 == c2 ? tr : R(0));
+      }
+      if (c == 0) {
+#pragma unroll
+        for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+          for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].set(K[c1][c2]);
+      } else {
+#pragma unroll
+        for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+          for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].add(K[c1][c2]);
+      }
+      if (diag) {
+        const int slot = HEX ? (int)kRuleHex8 : rule_slot_of(type, P.tet_nq);
+        R rb = R(0);
+        for (int q = 0; q < nq; ++q) {
+          R Nqa;
+          if constexpr (PREC == FEA_FP64)
+            Nqa = P.Ntab64[slot][q][a];
+          else
+            Nqa = P.Ntab[slot][q][a];
+          rb += ld_rec<STAGE>(re + kRecW + q) * Nqa;
+        }
+        if constexpr (OP == FEA_OP_DIFFUSION)
+          bacc[0].add(rb * (R)P.src);
+        else
+#pragma unroll
+          for (int c1 = 0; c1 < 3; ++c1) bacc[c1].add(rb * (R)P.f[c1]);
+      }
+    }
+    // the entry block, rounded once, to row i and transposed to row j
+    double v[D][D];
+#pragma unroll
+    for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+      for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
+    // complete entries are stored; block-boundary entries (block-task plan)
+    // are added to A with FP64 atomics
+    const bool at = T.flags & kTaskAtomicA;
+#pragma unroll
+    for (int c1 = 0; c1 < D; ++c1) {
+      const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
+#pragma unroll
+      for (int c2 = 0; c2 < D; ++c2) {
+        if (at)
+          atomicAdd(P.A + base + c2, v[c1][c2]);
+        else
+          P.A[base + c2] = v[c1][c2];
+      }
+    }
+    if (T.flags & kTaskTranspose) {
+#pragma unroll
+      for (int c2 = 0; c2 < D; ++c2) {
+        const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
+#pragma unroll
+        for (int c1 = 0; c1 < D; ++c1) {
+          if (at)
+            atomicAdd(P.A + base + c1, v[c1][c2]);
+          else
+            P.A[base + c1] = v[c1][c2];
+        }
+      }
+    }
+    if (diag) {
+      const int64_t gi = lnodes[T.li];
+#pragma unroll
+      for (int c1 = 0; c1 < D; ++c1) {
+        if (T.flags & kTaskAtomicB)
+          atomicAdd(P.b + D * gi + c1, bacc[c1].value());
+        else
+          P.b[D * gi + c1] = bacc[c1].value();
+      }
+    }
+  }
+}
+
+// STAGE: the halo elements' records are bulk-copied into shared memory (FP32).
+// GEO (with STAGE and HEX): the CTA computes them there from the mesh instead.
+template <int OP, int PREC, bool HEX, bool STAGE, bool GEO = false>
 __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant__ RowsArgs P) {
+  static_assert(!GEO || (STAGE && HEX), "fused geometry computes staged hex records");
   using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
   constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
   static_assert(!STAGE || PREC != FEA_FP64, "records are staged in FP32 only");
@@ -142,7 +348,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
   for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, parity ^= 1u) {
     const RowBlock H = P.blocks[blk];
     if (threadIdx.x < 32) {
-      const uint32_t rec_bytes = STAGE ? (uint32_t)(4 * kRecStride) * H.n_helem : 0u;
+      const uint32_t rec_bytes = (STAGE && !GEO) ? (uint32_t)(4 * kRecStride) * H.n_helem : 0u;
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order earlier reads of the buffers
         mbar_expect_tx(s_bar, H.task_bytes + H.contrib_bytes + H.helem_bytes + rec_bytes);
@@ -150,7 +356,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
         if (H.contrib_bytes) bulk_copy_g2s(s_contrib, P.contrib + H.contrib_off, H.contrib_bytes, s_bar);
         if (H.helem_bytes) bulk_copy_g2s(s_hid, P.helem_id + H.helem_off, H.helem_bytes, s_bar);
       }
-      if constexpr (STAGE) {
+      if constexpr (STAGE && !GEO) {
         // one 832-byte record per halo element (16-byte aligned at both ends)
         __syncwarp();
         for (int h = threadIdx.x; h < H.n_helem; h += 32) {
@@ -162,6 +368,16 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
     const int32_t* lnodes = P.lnodes + H.lnode_off;
     for (int t = threadIdx.x; t < H.n_owned * D; t += blockDim.x)
       s_rs[t] = P.row_ptr[(int64_t)D * lnodes[t / D] + t % D];
+    if constexpr (GEO) {
+      // the block's elements, 32 at a time (8 threads each), while the task
+      // lists are still in flight
+      for (int h0 = 0; h0 < H.n_helem; h0 += 32) {
+        const int h = h0 + (threadIdx.x >> 3);
+        const bool valid = h < H.n_helem;
+        const int64_t id = valid ? (int64_t)P.helem_id[H.helem_off + h] : 0;
+        fused_hex_record(P, valid, id, reinterpret_cast<float*>(s_recs) + (size_t)(valid ? h : 0) * kRowsRecSmem);
+      }
+    }
     const bool landed = mbar_wait_bounded(s_bar, parity);
     if (__syncthreads_or(!landed)) {
       // the copy did not land within the bound: report, wait a last bounded
@@ -170,128 +386,96 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
       mbar_wait_bounded(s_bar, parity);
       return;
     }
-    const R lam = (R)P.lam, mu = (R)P.mu;
-    for (int t = threadIdx.x; t < H.n_tasks; t += blockDim.x) {
-      const RowTask T = s_tasks[t];
-      const bool diag = T.flags & kTaskDiag;
-      Acc<PREC> acc[D][D];
-      Acc<PREC> bacc[D];
-#pragma unroll 1
-      for (int c = 0; c < T.nc; ++c) {
-        const int code = s_contrib[T.coff + c];
-        const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
-        const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
-        const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
-        const R* re = STAGE ? s_recs + (size_t)h * kRowsRecSmem : rec + (int64_t)s_hid[h] * kRecStride;
-        const R* ga = re + 3 * a;
-        const R* gb = re + 3 * bn;
-        R K[D][D];
-        if constexpr (OP == FEA_OP_DIFFUSION) {
-          R s = R(0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (!HEX && q >= nq) break;
-            const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
-                    x2 = ld_rec<STAGE>(ga + 24 * q + 2);
-            const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
-                    y2 = ld_rec<STAGE>(gb + 24 * q + 2);
-            s += ld_rec<STAGE>(re + kRecK + q) * (x0 * y0 + x1 * y1 + x2 * y2);
-          }
-          K[0][0] = s;
-        } else {
-          R M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (!HEX && q >= nq) break;
-            const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
-                    x2 = ld_rec<STAGE>(ga + 24 * q + 2);
-            const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
-                    y2 = ld_rec<STAGE>(gb + 24 * q + 2);
-            M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
-            M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
-            M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
-          }
-          const R tr = mu * (M[0][0] + M[1][1] + M[2][2]);
-#pragma unroll
-          for (int c1 = 0; c1 < 3; ++c1)
-#pragma unroll
-            for (int c2 = 0; c2 < 3; ++c2) K[c1][c2] = lam * M[c1][c2] + mu * M[c2][c1] + (c1 == c2 ? tr : R(0));
-        }
-        if (c == 0) {
-#pragma unroll
-          for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].set(K[c1][c2]);
-        } else {
-#pragma unroll
-          for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].add(K[c1][c2]);
-        }
-        if (diag) {
-          const int slot = HEX ? (int)kRuleHex8 : rule_slot_of(type, P.tet_nq);
-          R rb = R(0);
-          for (int q = 0; q < nq; ++q) {
-            R Nqa;
-            if constexpr (PREC == FEA_FP64)
-              Nqa = P.Ntab64[slot][q][a];
-            else
-              Nqa = P.Ntab[slot][q][a];
-            rb += ld_rec<STAGE>(re + kRecW + q) * Nqa;
-          }
-          if constexpr (OP == FEA_OP_DIFFUSION)
-            bacc[0].add(rb * (R)P.src);
-          else
-#pragma unroll
-            for (int c1 = 0; c1 < 3; ++c1) bacc[c1].add(rb * (R)P.f[c1]);
-        }
-      }
-      // the entry block, rounded once, to row i and transposed to row j
-      double v[D][D];
-#pragma unroll
-      for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
-      // complete entries are stored; block-boundary entries (block-task plan)
-      // are added to A with FP64 atomics
-      const bool at = T.flags & kTaskAtomicA;
-#pragma unroll
-      for (int c1 = 0; c1 < D; ++c1) {
-        const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
-#pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) {
-          if (at)
-            atomicAdd(P.A + base + c2, v[c1][c2]);
-          else
-            P.A[base + c2] = v[c1][c2];
-        }
-      }
-      if (T.flags & kTaskTranspose) {
-#pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) {
-          const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
-#pragma unroll
-          for (int c1 = 0; c1 < D; ++c1) {
-            if (at)
-              atomicAdd(P.A + base + c1, v[c1][c2]);
-            else
-              P.A[base + c1] = v[c1][c2];
-          }
-        }
-      }
-      if (diag) {
-        const int64_t gi = lnodes[T.li];
-#pragma unroll
-        for (int c1 = 0; c1 < D; ++c1) {
-          if (T.flags & kTaskAtomicB)
-            atomicAdd(P.b + D * gi + c1, bacc[c1].value());
-          else
-            P.b[D * gi + c1] = bacc[c1].value();
-        }
-      }
-    }
+    run_tasks<OP, PREC, HEX, STAGE>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, lnodes, threadIdx.x, blockDim.x);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Block-task plans of hex meshes in FP32-integrate, pipelined: one persistent
+// CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
+// shared-memory stages.  Warps 0-3 (producers) fill stage i & 1 for block i:
+// the task lists by TMA bulk copy, the row starts, and the FP64-geometry
+// records of the block's elements; warps 4-11 (consumers) run the tasks of
+// block i - 1 meanwhile.  The stages are handed over by mbarriers: full[s]
+// (1 arrival with the copy bytes + 128 producer arrivals) and empty[s] (256
+// consumer arrivals).  Every wait is bounded; a timeout latches
+// FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
+// ---------------------------------------------------------------------------
+constexpr int kPipeProducers = 128;
+constexpr int kPipeConsumers = 256;
+
+template <int OP>
+__global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
+    k_block_pipe(const __grid_constant__ RowsArgs P, uint32_t stage_bytes) {
+  extern __shared__ __align__(128) unsigned char pipe_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(pipe_raw + 2 * stage_bytes);
+  uint64_t* empty = full + 2;
+  __shared__ int s_issued[2];
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) {
+    mbar_init_count(&full[0], kPipeProducers + 1);
+    mbar_init_count(&full[1], kPipeProducers + 1);
+    mbar_init_count(&empty[0], kPipeConsumers);
+    mbar_init_count(&empty[1], kPipeConsumers);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_issued[0] = s_issued[1] = 0;
+    s_fail = 0;
+  }
+  __syncthreads();
+  const bool producer = threadIdx.x < kPipeProducers;
+  int i = 0;
+  for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, ++i) {
+    if (*((volatile int*)&s_fail)) break;
+    const int s = i & 1;
+    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+    unsigned char* base = pipe_raw + (size_t)s * stage_bytes;
+    float* s_recs = reinterpret_cast<float*>(base + P.L.recs);
+    int64_t* s_rs = reinterpret_cast<int64_t*>(base + P.L.rs);
+    RowTask* s_tasks = reinterpret_cast<RowTask*>(base + P.L.tasks);
+    uint16_t* s_contrib = reinterpret_cast<uint16_t*>(base + P.L.contrib);
+    int32_t* s_hid = reinterpret_cast<int32_t*>(base + P.L.hid);
+    const RowBlock H = P.blocks[blk];
+    const int32_t* lnodes = P.lnodes + H.lnode_off;
+    constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
+    if (producer) {
+      // the consumers of block i - 2 have released this stage
+      if (i >= 2 && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
+        if (atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
+        break;
+      }
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
+        mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
+        if (H.task_bytes) bulk_copy_g2s(s_tasks, P.tasks + H.task_off, H.task_bytes, &full[s]);
+        if (H.contrib_bytes) bulk_copy_g2s(s_contrib, P.contrib + H.contrib_off, H.contrib_bytes, &full[s]);
+        if (H.helem_bytes) bulk_copy_g2s(s_hid, P.helem_id + H.helem_off, H.helem_bytes, &full[s]);
+        ++s_issued[s];
+      }
+      for (int t = threadIdx.x; t < H.n_owned * D; t += kPipeProducers)
+        s_rs[t] = P.row_ptr[(int64_t)D * lnodes[t / D] + t % D];
+      for (int h0 = 0; h0 < H.n_helem; h0 += kPipeProducers / 8) {
+        const int h = h0 + (threadIdx.x >> 3);
+        const bool valid = h < H.n_helem;
+        const int64_t id = valid ? (int64_t)P.helem_id[H.helem_off + h] : 0;
+        fused_hex_record(P, valid, id, s_recs + (size_t)(valid ? h : 0) * kRowsRecSmem);
+      }
+      mbar_arrive(&full[s]);
+    } else {
+      if (!mbar_wait_bounded(&full[s], ph)) {
+        if (atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
+        break;
+      }
+      run_tasks<OP, FEA_FP32_INTEGRATE, true, true>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, lnodes,
+                                                    (int)threadIdx.x - kPipeProducers, kPipeConsumers);
+      mbar_arrive(&empty[s]);
+    }
+  }
+  __syncthreads();
+  // after a timeout: let the bulk copies still in flight land before exit
+  if (threadIdx.x == 0 && s_fail)
+    for (int s = 0; s < 2; ++s)
+      if (s_issued[s] > 0) mbar_wait_bounded(&full[s], (uint32_t)((s_issued[s] - 1) & 1));
 }
 
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
@@ -304,13 +488,17 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
   int geo_launches = 0;
   rc = geometry_pass(op, m, s, &records, &geo_launches);
   if (rc) return rc;
-  rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s);
+  rc = launch_task_kernel(op, *plan, records, row_ptr, A, b, m->status, s, nullptr);
   if (rc == FEA_OK) *launched = geo_launches + 1;
   return rc;
 }
 
+bool fused_geometry(const fea_operator* op, const RowsPlan& RP) {
+  return op->precision == FEA_FP32_INTEGRATE && RP.all_hex;
+}
+
 int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* records, const int64_t* row_ptr,
-                       double* A, double* b, DevStatus* st, cudaStream_t s) {
+                       double* A, double* b, DevStatus* st, cudaStream_t s, const fea_mesh* m) {
   int rc = FEA_OK;
   RowsArgs P;
   std::memset(&P, 0, sizeof(P));
@@ -342,6 +530,31 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
         P.Ntab64[k][q][a] = rr.N[q][a];
       }
   }
+  const bool geo = m != nullptr && fused_geometry(op, RP);
+  if (geo) {
+    P.coords = m->coords;
+    P.conn_off = m->conn_off;
+    P.conn = m->conn;
+    P.k0 = op->k0;
+    P.k2 = op->k2;
+    P.diffusion = op->kind == FEA_OP_DIFFUSION;
+    P.hex = host_rule(kRuleHex8);
+  }
+  if (geo) {
+    const uint32_t stage_bytes = (P.L.bar + 127u) & ~127u;
+    const size_t pipe_smem = 2 * (size_t)stage_bytes + 32;
+    if (pipe_smem <= kRowsMaxSmem) {
+      int dev = 0, sms = 0;
+      FEA_CUDA(cudaGetDevice(&dev));
+      FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      const unsigned grid = (unsigned)std::min<int64_t>(RP.n_blocks, sms);
+      auto kern = op->kind == FEA_OP_DIFFUSION ? k_block_pipe<FEA_OP_DIFFUSION> : k_block_pipe<FEA_OP_ELASTICITY>;
+      FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem));
+      kern<<<grid, kPipeProducers + kPipeConsumers, pipe_smem, s>>>(P, stage_bytes);
+      FEA_CUDA(cudaGetLastError());
+      return FEA_OK;
+    }
+  }
   const size_t smem = P.L.total;
   if (smem > kRowsMaxSmem)
     return fail(FEA_ERR_UNSUPPORTED, "rows: a block needs " + std::to_string(smem) + " bytes of shared memory");
@@ -358,15 +571,17 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
       rc = hex ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP64, true, false>)
                : launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP64, false, false>);
     else
-      rc = hex ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, true, true>)
-               : launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, false, true>);
+      rc = geo   ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, true, true, true>)
+           : hex ? launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, true, true>)
+                 : launch(k_rows_assemble<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, false, true>);
   } else {
     if (op->precision == FEA_FP64)
       rc = hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP64, true, false>)
                : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP64, false, false>);
     else
-      rc = hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, true, true>)
-               : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, false, true>);
+      rc = geo   ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, true, true, true>)
+           : hex ? launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, true, true>)
+                 : launch(k_rows_assemble<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, false, true>);
   }
   return rc;
 }
