@@ -394,15 +394,17 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 // ---------------------------------------------------------------------------
 // Block-task plans of hex meshes in FP32-integrate, pipelined: one persistent
 // CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
-// shared-memory stages.  Warps 0-3 (producers) fill stage i & 1 for block i:
+// shared-memory stages.  Warps 0-5 (producers) fill stage i & 1 for block i:
 // the task lists by TMA bulk copy, the row starts, and the FP64-geometry
-// records of the block's elements; warps 4-11 (consumers) run the tasks of
+// records of the block's elements; warps 6-13 (consumers) run the tasks of
 // block i - 1 meanwhile.  The stages are handed over by mbarriers: full[s]
-// (1 arrival with the copy bytes + 128 producer arrivals) and empty[s] (256
-// consumer arrivals).  Every wait is bounded; a timeout latches
+// (1 arrival with the copy bytes + 192 producer arrivals) and empty[s] (256
+// consumer arrivals).  Six producer warps keep up with eight consumer warps on
+// a hex mesh (measured: 4 producer warps leave the consumers waiting, 8 cost
+// registers).  Every wait is bounded; a timeout latches
 // FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
 // ---------------------------------------------------------------------------
-constexpr int kPipeProducers = 128;
+constexpr int kPipeProducers = 192;
 constexpr int kPipeConsumers = 256;
 
 template <int OP>
