@@ -45,7 +45,8 @@ METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, sam
 # ncu capture of the 64^3 case (same kernel and launch shape, inputs larger than
 # L2) scaled by the element count, which its traffic grows with.  Remove an
 # entry whenever its kernel changes.
-TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.969472e6 + 468.289792e6)}
+TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.969472e6 + 468.289792e6),
+                 "k_block_pipe": 8.0 * (417.433088e6 + 577.147136e6)}
 
 # the kernel each variant spends its step in
 DOMINANT_KERNEL = {"atomic": "k_assemble_tile", "color": "k_assemble_tile (one launch per color)",
@@ -332,7 +333,7 @@ def run_ours(args, rank, world, local_rank):
                 roof = {"bound": "hbm", "achieved": by / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                         "peak_source": peak_kind, "algorithmic_bytes": by}
         roof.update(frac=roof["achieved"] / roof["peak"], kernel=k_name, kernel_ms=k_ms,
-                    traffic=TRAFFIC_BYTES.get(k_name) if args.n == 128 else None)
+                    traffic=TRAFFIC_BYTES.get(k_name.split()[0]) if args.n == 128 else None)
         line = {
             "metric": METRIC,
             "value": whole_job_rate(E, world, r["ms_per_step"]),
