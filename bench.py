@@ -264,6 +264,24 @@ def run_ours(args, rank, world, local_rank):
         results[name] = dict(ms_per_step=total_ms / steps, kernel_ms=kern_ms, zero_ms=zero_ms, main_ms=main_ms,
                              geo_ms=geo_ms, launches=nk, steps=steps)
     clk = clocks.stop()
+    # the assembled operator applied to a vector (partial-row product, Sec. 3.1),
+    # on the system the last variant assembled: HBM-bound
+    spmv = None
+    if rank == 0:
+        x = torch.randn(sysm.b.numel(), dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        sp_ms = _time_calls(lambda: fea.fea_spmv(sysm.handle, 3, sysm.row_ptr, sysm.A, x, y), 20)
+        nnz_node = nnz // 9
+        sp_bytes = 8 * nnz + 4 * nnz_node + 8 * (N + 1) + 8 * N + 8 * 3 * N + 8 * 3 * N
+        hbm_pk, _ = _peaks()
+        # one FP64 FMA per stored value: on GB300 the FP64 pipe bounds the product
+        # about as tightly as HBM does, so both fractions are reported
+        p64 = NOMINAL_FP64_TFLOPS * 1e12
+        spmv = {"ms": sp_ms, "algorithmic_bytes": sp_bytes, "achieved_gbs": sp_bytes / (sp_ms * 1e-3) / 1e9,
+                "peak_gbs": hbm_pk, "frac": sp_bytes / (sp_ms * 1e-3) / 1e9 / hbm_pk,
+                "fp64_gflops": 2 * nnz / (sp_ms * 1e-3) / 1e9, "fp64_frac": 2 * nnz / (sp_ms * 1e-3) / p64,
+                "floor_ms": {"hbm": sp_bytes / (hbm_pk * 1e9) * 1e3, "fp64": 2 * nnz / p64 * 1e3},
+                "bytes": "A 8 nnz, node columns 4 nnz/9, node row starts, row_ptr (one per node), x and y once"}
     fp32 = [k for k in results if k.startswith("fp32_")]
     head = args.variant if args.variant in results else min(fp32, key=lambda k: results[k]["ms_per_step"])
 
@@ -364,6 +382,7 @@ def run_ours(args, rank, world, local_rank):
             "pattern_build_s": pattern_s,
             "first_call_s": plan_s,
             "rows_plan": fea.fea_rows_plan_info(sysm.handle),
+            "spmv": spmv,
             "clocks": clk,
             "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s",
                     "h2d_bytes_per_step": int(coords_h.numel() * 8),

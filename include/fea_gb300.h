@@ -292,6 +292,25 @@ int fea_element_loop(const fea_operator* op, fea_mesh* mesh, double* stress_d, v
 /* Grid size of the persistent element loop (as fea_persistent_grid). */
 int fea_element_loop_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
 
+/* Product of an assembled system with a vector, and the partial-row form of
+ * Sec. 3.1: with the elements partitioned into subdomains that each assemble
+ * the square local matrix of their own elements, y = sum_p P_p^T A_p P_p x,
+ * the interface rows being summed over the subdomains that hold the node.
+ *  mesh, ndof   the mesh (its node graph built for ndof by fea_pattern_size)
+ *  row_ptr_d, A_d  its assembled system (fea_build_csr_pattern / fea_assemble)
+ *  x_d, y_d     float64 vectors, ndof values per node (device)
+ *  glob_d       NULL: x and y are numbered like the mesh, y is overwritten.
+ *               Else int32 [n_nodes] local -> global node ids: x is gathered
+ *               and y scattered by them, and
+ *  shared_d     uint8 [n_nodes] (needed with glob_d): 1 for a node held by
+ *               other subdomains too -- its rows are added to y with FP64
+ *               atomics (y must hold 0 there before the first subdomain) --
+ *               0 for a node of this subdomain only, whose rows are stored.
+ * The matrix is read through the mesh's node graph (no scalar column array).
+ * Stream-ordered. */
+int fea_spmv(fea_mesh* mesh, int ndof, const int64_t* row_ptr_d, const double* A_d, const double* x_d, double* y_d,
+             const int32_t* glob_d, const uint8_t* shared_d, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned cost model (the GPU counterpart of the paper's dynamic load
  * balancing, Sec. 4: element costs are not known a priori).  A small MLP,

@@ -98,6 +98,7 @@ def _load():
         "fea_item_features": (I32, [P, I32, P, P, P, P]),
         "fea_pack_lpt": (I32, [P, I64, I32, P, P, P]),
         "fea_element_loop": (I32, [ctypes.POINTER(fea_operator), P, P, P]),
+        "fea_spmv": (I32, [P, I32, P, P, P, P, P, P, P]),
         "fea_element_loop_grid": (I32, [ctypes.POINTER(fea_operator), P, ctypes.POINTER(I32)]),
         "fea_batch_create": (I32, [ctypes.POINTER(fea_operator), I32, P, ctypes.POINTER(P)]),
         "fea_batch_destroy": (I32, [P]),
@@ -387,6 +388,12 @@ class Batch:
         if self.handle:
             _check(_lib.fea_batch_destroy(self.handle))
             self.handle = None
+
+
+def fea_spmv(h, ndof: int, row_ptr, A, x, y, glob=None, shared=None, stream=None):
+    """y = A x through the mesh's node graph; with glob/shared, add a subdomain's partial rows into a global y."""
+    _check(_lib.fea_spmv(h, ndof, _dptr(row_ptr), _dptr(A), _dptr(x), _dptr(y), _dptr(glob), _dptr(shared),
+                         _stream(stream)))
 
 
 def fea_element_loop(op: "fea_operator", h, stress=None, stream=None):

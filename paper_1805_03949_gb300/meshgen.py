@@ -351,3 +351,36 @@ def j2_workload(n: int = 96, amplitude: float = 1.0, seed_mesh: int = 6, seed_u:
     """
     mesh = hex_cube(n, 0.2, seed_mesh)
     return mesh, fourier_displacement(mesh.coords, amplitude, seed=seed_u)
+
+
+def partition_elements(mesh: Mesh, parts: int):
+    """Element partition into `parts` subdomains of consecutive element-centroid
+    z order (slabs), as the partial-row decomposition of Sec. 3.1 uses them.
+
+    Returns a list of (submesh, glob): the submesh has the elements of one part
+    with its own node numbering (nodes in increasing global id), glob [n_local]
+    its local -> global node ids; and the multiplicity of every global node
+    (how many parts hold it).
+    """
+    off = mesh.conn_offsets
+    nn = np.diff(off)
+    cz = np.zeros(mesh.n_elems)
+    np.add.at(cz, np.repeat(np.arange(mesh.n_elems), nn), mesh.coords[mesh.conn, 2])
+    cz /= nn
+    order = np.argsort(cz, kind="stable")
+    chunks = np.array_split(order, parts)
+    mult = np.zeros(mesh.n_nodes, dtype=np.int32)
+    out = []
+    for ids in chunks:
+        ids = np.sort(ids)
+        cnt = nn[ids]
+        starts = off[ids]
+        idx = np.repeat(starts, cnt) + (np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt))
+        gconn = mesh.conn[idx]
+        glob = np.unique(gconn).astype(np.int32)
+        mult[glob] += 1
+        lconn = np.searchsorted(glob, gconn).astype(np.int32)
+        coff = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+        sub = Mesh(mesh.coords[glob].copy(), mesh.types[ids].copy(), coff, lconn, dict(mesh.meta, part_of=len(out)))
+        out.append((sub, glob))
+    return out, mult
