@@ -201,6 +201,8 @@ def run_ours(args, rank, world, local_rank):
         "fp64_rows": fea.make_operator(kind=1, precision=0, scatter=fea.FEA_SCATTER_ROWS, poisson=0.3),
         "fp32_color": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_COLOR, poisson=0.3),
         "fp32_block": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_BLOCK, poisson=0.3),
+        # commutative multidependences: subdomains of 128 elements under neighbour-set locks
+        "fp32_multidep": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_MULTIDEP, poisson=0.3),
         # FP32 geometry with the FP64 redo of distorted elements only (kappa_F(J) > 12)
         "fp32a_atomic": fea.make_operator(kind=1, precision=2, scatter=fea.FEA_SCATTER_ATOMIC, poisson=0.3),
         "fp32a_rows": fea.make_operator(kind=1, precision=2, scatter=fea.FEA_SCATTER_ROWS, poisson=0.3),

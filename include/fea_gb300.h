@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define FEA_ABI_VERSION 2
+#define FEA_ABI_VERSION 3
 
 typedef enum {
   FEA_OK = 0,
@@ -90,12 +90,25 @@ typedef enum {
   FEA_SCATTER_COLOR = 1,  /* element coloring, plain read-modify-write per color (Alg. "coloring") */
   FEA_SCATTER_BLOCK = 2,  /* locality blocks accumulated in shared memory, block-boundary
                              entries resolved globally (Alg. "local partitioning" / "multideps") */
-  FEA_SCATTER_ROWS = 3    /* owner-computes full rows (Sec. 3.1 full-row decomposition with halo
+  FEA_SCATTER_ROWS = 3,   /* owner-computes full rows (Sec. 3.1 full-row decomposition with halo
                              elements, applied per CTA): each CTA owns a block of nodes along a
                              Morton curve, recomputes the geometry of the elements touching them and
                              writes every entry of its rows once with plain stores -- no atomics, no
                              zero fill, bitwise reproducible.  The first call per (mesh, ndof) builds
                              the block plan on the host (synchronous); later calls are stream-ordered. */
+  FEA_SCATTER_MULTIDEP = 4 /* commutative multidependences (Sec. 3.2.2, Alg. "multideps"): the
+                             elements are cut into subdomains of `chunk` consecutive elements of one
+                             type (the work items of fea_work_items); one persistent launch in which
+                             a CTA runs a subdomain only while it holds a lock on every subdomain of
+                             the subdomain's neighbour list (the subdomains sharing a node with it,
+                             itself included), so two subdomains whose lists meet never run at the
+                             same time, in no fixed order.  Locks are taken by bounded try-locks
+                             (all or none), subdomains with more neighbours first.  A subdomain's
+                             elements run in local color classes (no two elements of a class share
+                             a node) and add into A and b by plain read-modify-write: no atomics.
+                             A CTA that finds no subdomain it can take for lock_timeout_us latches
+                             FEA_ERR_TIMEOUT and exits.  The first call per (mesh, chunk) builds the
+                             plan on the host (synchronous).  Diffusion and elasticity only. */
 } fea_scatter;
 
 /* Scheduling of the element loop (the GPU counterpart of the paper's dynamic
@@ -148,7 +161,8 @@ typedef struct {
  *             events[1] after zeroing, events[2 + j] after the j-th kernel it
  *             launches (only those with index < n_events are recorded).
  *  schedule   fea_schedule (FEA_SCATTER_ATOMIC only for the persistent ones)
- *  chunk      elements per work item (persistent schedules; 0 = 128)
+ *  chunk      elements per work item (persistent schedules) and per subdomain
+ *             (FEA_SCATTER_MULTIDEP); 0 = 128
  *  n_ctas     persistent grid size (0 = the resident-CTA count); the queue schedules need it
  *  queue_d, queue_off_d  FEA_SCHED_QUEUES*: int32 item ids and int64 [n_ctas + 1]
  *             offsets (device); every item must appear exactly once (not checked)
@@ -198,6 +212,12 @@ typedef struct {
   double* state_out_d;
   uint8_t* yield_out_d;
   uint8_t* iters_out_d;
+  /* FEA_SCATTER_MULTIDEP */
+  int32_t lock_timeout_us;   /* bounded wait of a CTA that finds no subdomain to take (0 = 1 s) */
+  int32_t reserved4;
+  uint64_t* span_d;          /* optional uint64 [n_subdomains][2] (device): the %globaltimer
+                                nanoseconds at which each subdomain's locks were taken and at which
+                                its last add was done, before the release */
 } fea_operator;
 
 typedef struct fea_mesh fea_mesh;
@@ -453,6 +473,30 @@ int fea_mesh_set_block_elems(fea_mesh* mesh, int block_elems);
  * contributions, [6] halo elements (with repeats), [7] plan bytes on the
  * device.  Host call. */
 int fea_rows_plan_info(const fea_mesh* mesh, int64_t info[8]);
+
+/* The FEA_SCATTER_MULTIDEP plan for subdomains of `chunk` elements (0 = 128),
+ * built if the mesh holds none for that chunk (host work, synchronous).
+ *  info        int64 [4]: subdomains, neighbour-list entries, largest list,
+ *              most local colors of a subdomain
+ *  nb_off_h    NULL or int64 [subdomains + 1] (host): offsets into nb_h
+ *  nb_h        NULL or int32 [entries] (host): the neighbour list of each
+ *              subdomain, ascending, itself included (the locks it takes)
+ *  order_h     NULL or int32 [subdomains] (host): the priority order
+ *              (neighbour count descending; ties in a hashed order)
+ *  color_h     NULL or int32 [n_elems] (host): local color of each element
+ *              (original id) inside its subdomain
+ * Subdomain k is work item k of fea_work_items(chunk).  FEA_ERR_UNSUPPORTED
+ * if a subdomain would need more than 64 local colors. */
+int fea_multidep_plan(fea_mesh* mesh, int chunk, int64_t info[4], int64_t* nb_off_h, int32_t* nb_h, int32_t* order_h,
+                      int32_t* color_h);
+
+/* Hold (held = 1) or free (0) the lock of one subdomain of the mesh's
+ * FEA_SCATTER_MULTIDEP plan in every later launch, as if a CTA that never
+ * finishes owned it: the subdomains whose lists contain it can then never
+ * run, and the CTAs give up after lock_timeout_us with FEA_ERR_TIMEOUT.  For
+ * tests of the bounded wait.  Host call; FEA_ERR_ARG without a plan or for a
+ * subdomain out of range. */
+int fea_multidep_hold(fea_mesh* mesh, int subdomain, int held);
 
 /* The element coloring of FEA_SCATTER_COLOR (built by the first COLOR
  * assembly): *n_colors classes, and, if colors_h is not NULL, the class of

@@ -515,17 +515,44 @@ __device__ __forceinline__ void tile_body(typename TileCfg<TYPE, SLOT, OP, PREC,
     int64_t rb[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) rb[c] = P.row_ptr[D * node + c];
+    if constexpr (SC == FEA_SCATTER_MULTIDEP) {
+      // this thread is the only writer of these entries (subdomain locks and
+      // a local color class), but CTAs on other SMs wrote them before the
+      // locks changed hands: read them from L2, a column's loads before its
+      // stores (wider groups measured slower: registers)
 #pragma unroll
-    for (int bb = 0; bb < NB; ++bb) {
-      const int64_t k = mp[bb];
+      for (int bb = 0; bb < NB; ++bb) {
+        const int64_t k = mp[bb];
+        double old[D][D];
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+        for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int cc = 0; cc < D; ++cc) scatter_add<SC>(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
+          for (int cc = 0; cc < D; ++cc) old[c][cc] = __ldcg(P.A + rb[c] + D * k + cc);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int cc = 0; cc < D; ++cc) __stcg(P.A + rb[c] + D * k + cc, old[c][cc] + widen(K[bb][c][cc]));
+      }
+      if (b0 == 0) {
+        double ob[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) ob[c] = __ldcg(P.b + D * node + c);
+#pragma unroll
+        for (int c = 0; c < D; ++c) __stcg(P.b + D * node + c, ob[c] + widen(rhs[c]));
+      }
+    } else {
+#pragma unroll
+      for (int bb = 0; bb < NB; ++bb) {
+        const int64_t k = mp[bb];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int cc = 0; cc < D; ++cc) scatter_add<SC>(P.A + rb[c] + D * k + cc, widen(K[bb][c][cc]));
+      }
+      if (b0 == 0)
+#pragma unroll
+        for (int c = 0; c < D; ++c) scatter_add<SC>(P.b + D * node + c, widen(rhs[c]));
     }
-    if (b0 == 0)
-#pragma unroll
-      for (int c = 0; c < D; ++c) scatter_add<SC>(P.b + D * node + c, widen(rhs[c]));
   }
   __syncthreads();
 }
@@ -564,12 +591,12 @@ struct PersistCfg {
          mx(bytes<FEA_PRISM6, kRulePrism6, S2>(), bytes<FEA_HEX8, kRuleHex8, S2>()));
 };
 
-template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC = FEA_SCATTER_ATOMIC>
 __device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams& P, int64_t first, int64_t end) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   auto& sm = *reinterpret_cast<typename Cfg::Smem*>(raw);
   for (int64_t e0 = first; e0 < end; e0 += Cfg::EPC)
-    tile_body<TYPE, SLOT, OP, PREC, SPLIT, FEA_SCATTER_ATOMIC>(sm, c_rules[SLOT], P, e0, end);
+    tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC>(sm, c_rules[SLOT], P, e0, end);
 }
 
 // ONLY >= 0: every item uses that rule slot (a single-type mesh), so the
@@ -612,6 +639,144 @@ __global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ Pers
       }
     }
     sched_record(A.S, item, it.entry, t0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// commutative multidependences (FEA_SCATTER_MULTIDEP, Sec. 3.2.2): a CTA runs
+// a subdomain only while it holds the lock of every subdomain of its
+// neighbour list; the plan comes from multidep.cu
+// ---------------------------------------------------------------------------
+struct MdepArgs {
+  AsmParams table[kNumTypes];  // entry t: the group of element type t, launch list = the plan's
+  int32_t slot[kNumTypes];
+  const WorkItem* items;       // subdomain k: elements first .. first + count of type entry
+  const int64_t* nb_off;
+  const int32_t* nb;           // neighbour lists, ascending, each with itself
+  const int32_t* order;        // priority order
+  const int64_t* cb_off;
+  const int32_t* cb;           // color-class bounds (launch-list positions) per subdomain
+  int32_t* state;              // 0 pending, 1 taken, 2 done
+  int32_t* locks;              // 0 free
+  int32_t* ctrl;               // [0] scan hint: no position before it is pending; [1] done count
+  uint64_t* span;
+  DevStatus* st;
+  uint64_t timeout_ns;
+  int32_t n_sub;
+};
+
+constexpr int kMdepWindows = 16;  // windows of 32 candidates one scan looks at
+
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One lane: take subdomain k with every lock of its list (in ascending
+// order), or give back what it took and hold nothing.
+__device__ __forceinline__ bool mdep_try_take(const MdepArgs& A, int k) {
+  if (atomicCAS(&A.state[k], 0, 1) != 0) return false;
+  const int64_t j0 = A.nb_off[k], j1 = A.nb_off[k + 1];
+  for (int64_t j = j0; j < j1; ++j) {
+    if (atomicCAS(&A.locks[A.nb[j]], 0, 1) != 0) {
+      for (int64_t i = j0; i < j; ++i) atomicExch(&A.locks[A.nb[i]], 0);
+      atomicExch(&A.state[k], 0);
+      return false;
+    }
+  }
+  __threadfence();  // the locks are ours before any read of A
+  return true;
+}
+
+// Warp 0 of the CTA: the next subdomain it runs, every lock of its list
+// held (>= 0); -1 once every subdomain is done; -2 after searching in vain
+// for longer than the timeout.  A scan walks the priority order in windows
+// of 32 from the CTA's cursor (the hint when it starts over): lanes that see
+// a pending subdomain whose locks all look free try to take it, lowest
+// position first.  The hint moves over finished subdomains.
+__device__ int mdep_next(const MdepArgs& A, int& cursor) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (ld_relaxed(&A.ctrl[1]) >= A.n_sub) return -1;
+    const int h = ld_relaxed(&A.ctrl[0]);
+    if (cursor < h || cursor >= A.n_sub) cursor = h;
+    bool prefix = cursor == h;
+    for (int w = 0; w < kMdepWindows && cursor < A.n_sub; ++w, cursor += 32) {
+      const int pos = cursor + lane;
+      int k = -1, st = 2;
+      if (pos < A.n_sub) {
+        k = A.order[pos];
+        st = ld_relaxed(&A.state[k]);
+      }
+      const unsigned open = __ballot_sync(0xffffffffu, st != 2);
+      if (prefix) {
+        const int first = open ? cursor + __ffs(open) - 1 : (cursor + 32 < A.n_sub ? cursor + 32 : A.n_sub);
+        if (lane == 0 && first > h) atomicMax(&A.ctrl[0], first);
+        prefix = open == 0;
+      }
+      int busy = st != 0;
+      if (!busy)
+        for (int64_t j = A.nb_off[k]; j < A.nb_off[k + 1]; ++j) busy |= ld_relaxed(&A.locks[A.nb[j]]);
+      unsigned m = __ballot_sync(0xffffffffu, !busy);
+      while (m) {
+        const int L = __ffs(m) - 1;
+        m &= m - 1;
+        int got = 0;
+        if (lane == L) got = mdep_try_take(A, k);
+        if (__shfl_sync(0xffffffffu, got, L)) return __shfl_sync(0xffffffffu, k, L);
+      }
+    }
+    if (global_ns() - t0 > A.timeout_ns) return -2;
+    __nanosleep(500);
+  }
+}
+
+template <int OP, int PREC, int ONLY>
+__global__ void __launch_bounds__(128) k_multidep(const __grid_constant__ MdepArgs A) {
+  constexpr int S2 = PersistCfg<OP, PREC>::S2;
+  constexpr int MD = FEA_SCATTER_MULTIDEP;
+  extern __shared__ __align__(16) unsigned char mdep_smem[];
+  __shared__ int s_sub;
+  int cursor = 0;
+  for (;;) {
+    if (threadIdx.x < 32) {
+      const int k = mdep_next(A, cursor);
+      if (threadIdx.x == 0) {
+        if (k == -2) latch_error(A.st, FEA_ERR_TIMEOUT, (unsigned long long)blockIdx.x);
+        if (k >= 0 && A.span) A.span[2 * k] = global_ns();
+        s_sub = k;
+      }
+    }
+    __syncthreads();
+    const int k = s_sub;
+    if (k < 0) break;
+    const WorkItem w = A.items[k];
+    const AsmParams& P = A.table[w.entry];
+    // the subdomain's local color classes, one after the other
+    for (int64_t c = A.cb_off[k]; c + 1 < A.cb_off[k + 1]; ++c) {
+      const int64_t p0 = A.cb[c], p1 = A.cb[c + 1];
+      if constexpr (ONLY == kRuleHex8) {
+        persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2, MD>(mdep_smem, P, p0, p1);
+      } else {
+        switch (A.slot[w.entry]) {
+          case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1, MD>(mdep_smem, P, p0, p1); break;
+          case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1, MD>(mdep_smem, P, p0, p1); break;
+          case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1, MD>(mdep_smem, P, p0, p1); break;
+          case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2, MD>(mdep_smem, P, p0, p1); break;
+          default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2, MD>(mdep_smem, P, p0, p1); break;
+        }
+      }
+    }
+    __syncthreads();  // every add of the subdomain is issued
+    if (threadIdx.x == 0) {
+      if (A.span) A.span[2 * k + 1] = global_ns();
+      __threadfence();  // ... and visible before the locks change hands
+      for (int64_t j = A.nb_off[k]; j < A.nb_off[k + 1]; ++j) atomicExch(&A.locks[A.nb[j]], 0);
+      atomicExch(&A.state[k], 2);
+      atomicAdd(&A.ctrl[1], 1);
+    }
   }
 }
 
@@ -756,6 +921,80 @@ int launch_persistent_assemble(const fea_operator* op, fea_mesh* m, const int64_
   return rc;
 }
 
+template <int OP, int PREC, int ONLY>
+static int launch_multidep_k(const MdepArgs& args, int n_ctas, cudaStream_t s) {
+  constexpr size_t smem = ONLY == kRuleHex8 ? sizeof(typename TileCfg<FEA_HEX8, kRuleHex8, OP, PREC,
+                                                                       PersistCfg<OP, PREC>::S2>::Smem)
+                                            : PersistCfg<OP, PREC>::smem;
+  auto kern = k_multidep<OP, PREC, ONLY>;
+  if (smem > 48 * 1024) FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = n_ctas;
+  if (grid <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    FEA_CUDA(cudaGetDevice(&dev));
+    FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FEA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid > args.n_sub) grid = args.n_sub;
+  kern<<<grid, 128, smem, s>>>(args);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
+// One persistent launch over the subdomains of the plan (A and b zeroed by
+// the caller, the plan's state reset on the stream here).
+int launch_multidep(const fea_operator* op, fea_mesh* m, const MultidepPlan& plan, const int64_t* row_ptr,
+                    const int32_t* node_map, double* A, double* b, cudaStream_t s) {
+  if (plan.n_sub == 0) return FEA_OK;
+  int rc = init_rule_constants();
+  if (rc) return rc;
+  rc = reset_multidep(plan, s);
+  if (rc) return rc;
+  MdepArgs args;
+  std::memset(&args, 0, sizeof(args));
+  const AsmParams base = base_params(op, m, row_ptr, node_map, A, b);
+  for (int t = 0; t < kNumTypes; ++t) {
+    args.table[t] = base;
+    const TypeGroup& g = m->group[t];
+    args.table[t].tconn = g.conn;
+    args.table[t].ids = g.ids;
+    args.table[t].mapoff = g.mapoff;
+    args.table[t].list = plan.lists[t];
+    args.table[t].n = g.n;
+    args.slot[t] = rule_slot_of(t, op->tet_rule);
+  }
+  args.items = plan.items;
+  args.nb_off = plan.nb_off;
+  args.nb = plan.nb;
+  args.order = plan.order;
+  args.cb_off = plan.cb_off;
+  args.cb = plan.cb;
+  args.state = plan.state;
+  args.locks = plan.locks;
+  args.ctrl = plan.ctrl;
+  args.span = op->span_d;
+  args.st = m->status;
+  args.timeout_ns = 1000ull * (uint64_t)(op->lock_timeout_us > 0 ? op->lock_timeout_us : 1000000);
+  args.n_sub = (int32_t)plan.n_sub;
+  bool hex_only = m->group[FEA_HEX8].n > 0;
+  for (int t = 0; t < kNumTypes; ++t)
+    if (t != FEA_HEX8 && m->group[t].n) hex_only = false;
+  const bool f64 = op->precision == FEA_FP64;
+  if (op->kind == FEA_OP_DIFFUSION) {
+    if (hex_only)
+      return f64 ? launch_multidep_k<FEA_OP_DIFFUSION, FEA_FP64, kRuleHex8>(args, op->n_ctas, s)
+                 : launch_multidep_k<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, kRuleHex8>(args, op->n_ctas, s);
+    return f64 ? launch_multidep_k<FEA_OP_DIFFUSION, FEA_FP64, -1>(args, op->n_ctas, s)
+               : launch_multidep_k<FEA_OP_DIFFUSION, FEA_FP32_INTEGRATE, -1>(args, op->n_ctas, s);
+  }
+  if (hex_only)
+    return f64 ? launch_multidep_k<FEA_OP_ELASTICITY, FEA_FP64, kRuleHex8>(args, op->n_ctas, s)
+               : launch_multidep_k<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, kRuleHex8>(args, op->n_ctas, s);
+  return f64 ? launch_multidep_k<FEA_OP_ELASTICITY, FEA_FP64, -1>(args, op->n_ctas, s)
+             : launch_multidep_k<FEA_OP_ELASTICITY, FEA_FP32_INTEGRATE, -1>(args, op->n_ctas, s);
+}
+
 // ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
@@ -801,7 +1040,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
   if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE && op->precision != FEA_FP32_ADAPTIVE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
-  if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_ROWS)
+  if (op->scatter < FEA_SCATTER_ATOMIC || op->scatter > FEA_SCATTER_MULTIDEP)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown scatter variant");
   if (op->tet_rule != 0 && op->tet_rule != 1) return fail(FEA_ERR_ARG, "fea_assemble: tet_rule must be 0 or 1");
   if (op->schedule < FEA_SCHED_PER_TYPE || op->schedule > FEA_SCHED_QUEUES_STEAL)
@@ -809,6 +1048,27 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
   const int D = op->kind == FEA_OP_DIFFUSION ? 1 : 3;
   if (m->pattern_ndof != D || !m->pattern_built)
     return fail(FEA_ERR_ARG, "fea_assemble: build the pattern and map for ndof = " + std::to_string(D) + " first");
+  if (op->scatter == FEA_SCATTER_MULTIDEP) {
+    // its own persistent launch over the subdomains (the schedule is not used)
+    if (op->kind == FEA_OP_J2) return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: FEA_SCATTER_MULTIDEP assembles diffusion and elasticity");
+    if (op->kind == FEA_OP_ELASTICITY && !(op->poisson > -1.0 && op->poisson < 0.5))
+      return fail(FEA_ERR_ARG, "fea_assemble: poisson must be in (-1, 0.5)");
+    if (op->chunk < 0 || op->n_ctas < 0 || op->lock_timeout_us < 0)
+      return fail(FEA_ERR_ARG, "fea_assemble: chunk, n_ctas and lock_timeout_us must be >= 0");
+    MultidepPlan* plan = nullptr;
+    int rc = ensure_multidep_plan(m, op->chunk > 0 ? op->chunk : 128, &plan);  // host work on the first call only
+    if (rc) return rc;
+    cudaEvent_t* ev = (cudaEvent_t*)op->events;
+    const int nev = ev ? op->n_events : 0;
+    if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
+    FEA_CUDA(cudaMemsetAsync(A, 0, (int64_t)D * D * m->nnz_node * sizeof(double), s));
+    FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
+    if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
+    rc = launch_multidep(op, m, *plan, row_ptr, node_map, A, b, s);
+    if (rc) return rc;
+    for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
+    return FEA_OK;
+  }
   if (op->schedule != FEA_SCHED_PER_TYPE) return assemble_persistent(op, m, row_ptr, node_map, A, b, s);
   if (op->kind == FEA_OP_J2) return assemble_j2(op, m, row_ptr, node_map, A, b, s);
   if (op->kind == FEA_OP_ELASTICITY) {
@@ -932,8 +1192,8 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
 
 int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
   if (!op || !m || !n) return fail(FEA_ERR_ARG, "fea_assemble_launches: null argument");
-  if (op->schedule != FEA_SCHED_PER_TYPE) {
-    *n = 1;  // one persistent launch over every type
+  if (op->schedule != FEA_SCHED_PER_TYPE || op->scatter == FEA_SCATTER_MULTIDEP) {
+    *n = 1;  // one persistent launch over every type (or every subdomain)
     return FEA_OK;
   }
   if (op->scatter == FEA_SCATTER_ROWS || op->scatter == FEA_SCATTER_BLOCK) {

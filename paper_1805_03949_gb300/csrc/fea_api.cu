@@ -57,6 +57,7 @@ static void free_mesh(fea_mesh* m) {
   cudaFree(m->geo[1]);
   fea::free_sched(m);
   free_color_plan(m);
+  free_multidep_plan(m);
   if (m->blocks) {
     free_rows_plan(m->blocks);
     delete m->blocks;

@@ -42,6 +42,33 @@ struct ColorPlan {
   std::vector<int32_t> colors_host;  // color of every element (original ids)
 };
 
+// Subdomain plan of FEA_SCATTER_MULTIDEP (multidep.cu): subdomain k is work
+// item k of the chunk; its neighbour list (ascending, itself included) names
+// the locks it takes; its elements sit in list positions first .. first +
+// count of its type, grouped by local color (class c at cb[cb_off[k] + c] ..
+// cb[cb_off[k] + c + 1]).
+struct MultidepPlan {
+  int chunk = 0;
+  int64_t n_sub = 0;
+  int64_t max_nb = 0;
+  int max_colors = 0;
+  int held = -1;                        // a lock held in every launch (tests of the bounded wait)
+  std::vector<WorkItem> items_h;
+  std::vector<int64_t> nb_off_h, cb_off_h;
+  std::vector<int32_t> nb_h, order_h, cb_h, color_h;
+  std::vector<int32_t> lists_h[4];
+  WorkItem* items = nullptr;            // device copies
+  int64_t* nb_off = nullptr;
+  int32_t* nb = nullptr;
+  int32_t* order = nullptr;
+  int64_t* cb_off = nullptr;
+  int32_t* cb = nullptr;
+  int32_t* lists[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t* state = nullptr;             // [n_sub] 0 pending, 1 taken, 2 done (one allocation with:)
+  int32_t* locks = nullptr;             // [n_sub] 0 free
+  int32_t* ctrl = nullptr;              // [2] scan hint (priority position), subdomains done
+};
+
 // Per-type element group: original ids and packed connectivity.
 struct TypeGroup {
   int64_t n = 0;            // elements of this type
@@ -79,6 +106,7 @@ struct fea_mesh {
   void* geo[2] = {nullptr, nullptr};            // geometry records per precision (geometry.cu)
   fea::ColorPlan* color = nullptr;              // FEA_SCATTER_COLOR classes (color.cu)
   fea::RowsPlan* blocks = nullptr;              // FEA_SCATTER_BLOCK plan (blocks.cu)
+  fea::MultidepPlan* mdep = nullptr;            // FEA_SCATTER_MULTIDEP plan (multidep.cu)
   int block_elems = 64;                         // elements per block of FEA_SCATTER_BLOCK
   int rows_block_nodes = 64;
   // persistent schedules (persistent.cu): work items of the last chunk size
@@ -140,6 +168,13 @@ void batch_entry(const fea_operator* op, fea_mesh* m, int t, const int64_t* row_
 int init_rule_constants();     // __constant__ quadrature tables of the persistent kernels (current device)
 int init_rule_constants_j2();
 void free_sched(fea_mesh* m);
+
+// multidep.cu (host plan) and assemble.cu (its launch)
+int ensure_multidep_plan(fea_mesh* m, int chunk, MultidepPlan** out);
+void free_multidep_plan(fea_mesh* m);
+int reset_multidep(const MultidepPlan& P, cudaStream_t s);
+int launch_multidep(const fea_operator* op, fea_mesh* m, const MultidepPlan& plan, const int64_t* row_ptr,
+                    const int32_t* node_map, double* A, double* b, cudaStream_t s);
 
 // color.cu
 int build_color_plan(fea_mesh* m, cudaStream_t s);

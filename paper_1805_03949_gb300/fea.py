@@ -32,7 +32,7 @@ FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
 FEA_OP_DIFFUSION, FEA_OP_ELASTICITY, FEA_OP_J2 = 0, 1, 2
 FEA_SCHED_PER_TYPE, FEA_SCHED_STEAL, FEA_SCHED_QUEUES, FEA_SCHED_QUEUES_STEAL = 0, 1, 2, 3
 FEA_FP64, FEA_FP32_INTEGRATE, FEA_FP32_ADAPTIVE = 0, 1, 2
-FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS = 0, 1, 2, 3
+FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS, FEA_SCATTER_MULTIDEP = 0, 1, 2, 3, 4
 
 
 class FeaError(RuntimeError):
@@ -66,7 +66,8 @@ class fea_operator(ctypes.Structure):
                 ("hardening", ctypes.c_double), ("tol_g", ctypes.c_double), ("tol_step", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("reserved3", ctypes.c_int32),
                 ("u_d", ctypes.c_void_p), ("state_in_d", ctypes.c_void_p), ("state_out_d", ctypes.c_void_p),
-                ("yield_out_d", ctypes.c_void_p), ("iters_out_d", ctypes.c_void_p)]
+                ("yield_out_d", ctypes.c_void_p), ("iters_out_d", ctypes.c_void_p),
+                ("lock_timeout_us", ctypes.c_int32), ("reserved4", ctypes.c_int32), ("span_d", ctypes.c_void_p)]
 
 
 def _load():
@@ -114,6 +115,8 @@ def _load():
         "fea_rows_plan_info": (I32, [P, ctypes.POINTER(I64)]),
         "fea_color_info": (I32, [P, P, ctypes.POINTER(I32)]),
         "fea_mesh_set_block_elems": (I32, [P, I32]),
+        "fea_multidep_plan": (I32, [P, I32, ctypes.POINTER(I64), P, P, P, P]),
+        "fea_multidep_hold": (I32, [P, I32, I32]),
     }
     for name, (rt, at) in sig.items():
         f = getattr(lib, name)
@@ -252,6 +255,27 @@ def fea_color_info(h, n_elems: int):
     colors = np.zeros(n_elems, dtype=np.int32)
     _check(_lib.fea_color_info(h, ctypes.c_void_p(colors.ctypes.data), ctypes.byref(n)))
     return n.value, colors
+
+
+def fea_multidep_plan(h, chunk: int, n_elems: int) -> dict:
+    """The FEA_SCATTER_MULTIDEP plan of `chunk` (built if needed): counts,
+    neighbour lists (CSR), priority order and local colors (numpy)."""
+    info = (ctypes.c_int64 * 4)()
+    _check(_lib.fea_multidep_plan(h, int(chunk), info, None, None, None, None))
+    n_sub, n_nb = int(info[0]), int(info[1])
+    nb_off = np.zeros(n_sub + 1, dtype=np.int64)
+    nb = np.zeros(max(n_nb, 1), dtype=np.int32)
+    order = np.zeros(max(n_sub, 1), dtype=np.int32)
+    color = np.zeros(max(n_elems, 1), dtype=np.int32)
+    _check(_lib.fea_multidep_plan(h, int(chunk), info, ctypes.c_void_p(nb_off.ctypes.data),
+                                  ctypes.c_void_p(nb.ctypes.data), ctypes.c_void_p(order.ctypes.data),
+                                  ctypes.c_void_p(color.ctypes.data)))
+    return {"subdomains": n_sub, "entries": n_nb, "max_neighbours": int(info[2]), "max_colors": int(info[3]),
+            "nb_off": nb_off, "nb": nb[:n_nb], "order": order[:n_sub], "color": color[:n_elems]}
+
+
+def fea_multidep_hold(h, subdomain: int, held: bool):
+    _check(_lib.fea_multidep_hold(h, int(subdomain), 1 if held else 0))
 
 
 def fea_work_items(h, chunk: int = 0):
@@ -433,7 +457,7 @@ def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER
                   schedule=FEA_SCHED_PER_TYPE, chunk=0, n_ctas=0, queue=None, queue_off=None, item_ns=None,
                   item_cta=None, sigma0=1e-3, sigma_inf=3e-3, delta=300.0, hardening=1e-2, tol_g=1e-13,
                   tol_step=1e-15, max_iter=12, u=None, state_in=None, state_out=None, yield_out=None,
-                  iters_out=None) -> fea_operator:
+                  iters_out=None, lock_timeout_us=0, span=None) -> fea_operator:
     """Operator struct; tensors (device) are referenced by pointer, the caller keeps them alive."""
     op = fea_operator()
     op.kind, op.precision, op.scatter, op.tet_rule = kind, precision, scatter, tet_rule
@@ -448,6 +472,7 @@ def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER
     op.tol_g, op.tol_step, op.max_iter = tol_g, tol_step, max_iter
     op.u_d, op.state_in_d, op.state_out_d = _dptr(u), _dptr(state_in), _dptr(state_out)
     op.yield_out_d, op.iters_out_d = _dptr(yield_out), _dptr(iters_out)
+    op.lock_timeout_us, op.span_d = lock_timeout_us, _dptr(span)
     return op
 
 

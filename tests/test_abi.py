@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(clib):
 
 def test_host_side_argument_checks(clib):
     clib.fea_abi_version.restype = ctypes.c_int
-    assert clib.fea_abi_version() == 2
+    assert clib.fea_abi_version() == 3
     clib.fea_last_error.restype = ctypes.c_char_p
     out = ctypes.c_void_p()
     rc = clib.fea_mesh_upload(None, None, ctypes.byref(out))
