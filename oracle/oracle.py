@@ -80,6 +80,9 @@ def _extra_signatures():
         "oracle_j2_element": (_i32, [_i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
         "oracle_j2_assemble": (_i64, [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
         "oracle_j2_sweep": (_i64, [_i64, _p, _p, _p, _p, _p, _p, ctypes.c_double, _p, _p, _p, _p, _p]),
+        "oracle_nh_point": (_i32, [_p, _p, _p, _p, _p]),
+        "oracle_nh_element": (_i32, [_i32, _p, _p, _p, _p, _p, _p, _p, _p]),
+        "oracle_nh_assemble": (_i64, [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
     }
 
 
@@ -342,3 +345,58 @@ def j2_points(mesh, U, state_n=None, **kw):
     if n < 0:
         raise NoConvergence("inverted element or failed return map")
     return dict(state=st, stress=sig, iters=it, yielded=yl, n_yielded=int(n))
+
+
+# ---------------------------------------------------------------------------
+# finite-strain neo-Hookean solid (nh_oracle.c)
+# ---------------------------------------------------------------------------
+
+def nh_params(young=1.0, poisson=0.3, mass=0.0) -> np.ndarray:
+    """E, nu and the Newmark mass coefficient m = rho0 / (beta dt^2)."""
+    return np.array([young, poisson, mass], dtype=np.float64)
+
+
+def nh_point(F, **kw):
+    """First Piola-Kirchhoff stress P [3, 3], tangent dP/dF [3, 3, 3, 3] and energy density at F."""
+    prm = nh_params(**kw)
+    F = _c(F, np.float64)
+    P = np.zeros(9); At = np.zeros(81); psi = ctypes.c_double()
+    if lib().oracle_nh_point(_ptr(prm), _ptr(F), _ptr(P), _ptr(At), ctypes.byref(psi)):
+        raise InvertedElement(-1)
+    return dict(P=P.reshape(3, 3), A=At.reshape(3, 3, 3, 3), psi=psi.value)
+
+
+def nh_element(etype, X, U, **kw):
+    """Jacobian, internal force, normwise scales and stored energy of one element."""
+    prm = nh_params(**kw)
+    X = _c(X, np.float64); U = _c(U, np.float64)
+    n = 3 * NODES[etype]
+    Ae = np.zeros((n, n)); be = np.zeros(n); Ne = np.zeros((n, n)); Nb = np.zeros(n); en = ctypes.c_double()
+    rc = lib().oracle_nh_element(etype, _ptr(prm), _ptr(X), _ptr(U), _ptr(Ae), _ptr(be), _ptr(Ne), _ptr(Nb),
+                                 ctypes.byref(en))
+    if rc:
+        raise InvertedElement(-1)
+    return dict(A=Ae, b=be, NA=Ne, Nb=Nb, energy=en.value)
+
+
+def nh_assemble(mesh, U, pat=None, **kw):
+    """Jacobian and internal force of the whole mesh (3 dofs per node), element-index order.
+
+    U: [n_nodes, 3].  Returns dict(row_ptr, col_idx, node_map, A, b, NA, Nb, energy).
+    """
+    if pat is None:
+        pat = pattern(mesh, 3)
+    rps, cols, nmap = pat
+    prm = nh_params(**kw)
+    E = mesh.n_elems
+    A = np.zeros(cols.shape[0]); NA = np.zeros_like(A)
+    b = np.zeros(mesh.n_nodes * 3); Nb = np.zeros_like(b)
+    en = ctypes.c_double()
+    types = _c(mesh.types, np.uint8); off = _c(mesh.conn_offsets, np.int64); conn = _c(mesh.conn, np.int32)
+    coords = _c(mesh.coords, np.float64); U = _c(U, np.float64)
+    rc = lib().oracle_nh_assemble(mesh.n_nodes, E, _ptr(types), _ptr(off), _ptr(conn), _ptr(coords), _ptr(prm),
+                                  _ptr(U), _ptr(rps), _ptr(nmap), _ptr(A), _ptr(b), _ptr(NA), _ptr(Nb),
+                                  ctypes.byref(en))
+    if rc < 0:
+        raise InvertedElement((-rc - 1) % E)
+    return dict(row_ptr=rps, col_idx=cols, node_map=nmap, A=A, b=b, NA=NA, Nb=Nb, energy=en.value)
