@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
                              geo_ms=geo_ms, launches=nk, steps=steps)
     clk = clocks.stop()
     # the assembled operator applied to a vector (partial-row product, Sec. 3.1),
-    # on the system the last variant assembled: HBM-bound
+    # on the system the last variant assembled
     spmv = None
     if rank == 0:
         x = torch.randn(sysm.b.numel(), dtype=torch.float64, device=dev)
@@ -284,6 +284,19 @@ def run_ours(args, rank, world, local_rank):
                 "fp64_gflops": 2 * nnz / (sp_ms * 1e-3) / 1e9, "fp64_frac": 2 * nnz / (sp_ms * 1e-3) / p64,
                 "floor_ms": {"hbm": sp_bytes / (hbm_pk * 1e9) * 1e3, "fp64": 2 * nnz / p64 * 1e3},
                 "bytes": "A 8 nnz, node columns 4 nnz/9, node row starts, row_ptr (one per node), x and y once"}
+    # the finite-strain solid (Sec. 2.2, neo-Hookean reading) on the same mesh:
+    # the Newton Jacobian and internal force at a smooth deformation
+    neo = None
+    if rank == 0:
+        from paper_1805_03949_gb300 import meshgen as mg
+        U = mg.fourier_displacement(mesh.coords, 0.004, seed=6) + 0.05 * mesh.coords[:, [1, 2, 0]]
+        u_d = torch.tensor(U.reshape(-1), device=dev)
+        neo = {"deformation": "fourier_displacement(0.004, seed 6) + 0.05 (y, z, x): strains of several %"}
+        for name, prec, steps in (("fp32_atomic", 1, 10), ("fp64_atomic", 0, 3)):
+            op = fea.make_operator(kind=fea.FEA_OP_NEOHOOKE, precision=prec, u=u_d, young=1.0, poisson=0.3)
+            ms = _time_calls(lambda: sysm.assemble(op), steps)
+            sysm.check()
+            neo[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3)}
     fp32 = [k for k in results if k.startswith("fp32_")]
     head = args.variant if args.variant in results else min(fp32, key=lambda k: results[k]["ms_per_step"])
 
@@ -385,6 +398,7 @@ def run_ours(args, rank, world, local_rank):
             "first_call_s": plan_s,
             "rows_plan": fea.fea_rows_plan_info(sysm.handle),
             "spmv": spmv,
+            "neohooke": neo,
             "clocks": clk,
             "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s",
                     "h2d_bytes_per_step": int(coords_h.numel() * 8),

@@ -63,10 +63,18 @@ typedef enum { FEA_TET4 = 0, FEA_PYR5 = 1, FEA_PRISM6 = 2, FEA_HEX8 = 3 } fea_el
 typedef enum {
   FEA_OP_DIFFUSION = 0,  /* scalar, 1 dof/node: A_ab = int k(x) grad N_a . grad N_b, b_a = int f N_a */
   FEA_OP_ELASTICITY = 1, /* 3 dofs/node, isotropic small strain: A = int B^T D B, b = int f N        */
-  FEA_OP_J2 = 2          /* 3 dofs/node, small-strain J2 plasticity with Voce hardening (the Gauss-point
+  FEA_OP_J2 = 2,         /* 3 dofs/node, small-strain J2 plasticity with Voce hardening (the Gauss-point
                             constitutive update of the solid element loop, Sec. 2.2 / 5.2): radial return
                             from the committed state, A = int B^T D_ep B with the consistent tangent,
                             b = f_int = int B^T sigma; see the J2 fields of fea_operator */
+  FEA_OP_NEOHOOKE = 3    /* 3 dofs/node, finite strain in the reference configuration (Sec. 2.2: first
+                            Piola-Kirchhoff stress P, Newton-Raphson on the Newmark-discretised momentum
+                            balance), compressible neo-Hookean solid (Bonet and Wood 2008, Sec. 6.4.3):
+                            Psi = mu/2 (F:F - 3) - mu ln J + lam/2 (ln J)^2, F = I + grad0 u at each Gauss
+                            point;  A = int grad0 N (dP/dF) grad0 N + mass int N N I  (the Jacobian),
+                            b = f_int = int P grad0 N.  Needs u_d; young, poisson, mass as documented in
+                            fea_operator; tet4 always 4-point; ATOMIC or COLOR scatter, per-type launches.
+                            det J0 <= 0 or det F <= 0 at a point latches FEA_ERR_INVERTED_ELEMENT. */
 } fea_op_kind;
 
 typedef enum {
@@ -218,6 +226,9 @@ typedef struct {
   uint64_t* span_d;          /* optional uint64 [n_subdomains][2] (device): the %globaltimer
                                 nanoseconds at which each subdomain's locks were taken and at which
                                 its last add was done, before the release */
+  /* FEA_OP_NEOHOOKE */
+  double mass;               /* m >= 0 of the Newmark Jacobian term m int N_a N_b I
+                                (m = rho0 / (beta dt^2); 0: a static Newton step) */
 } fea_operator;
 
 typedef struct fea_mesh fea_mesh;

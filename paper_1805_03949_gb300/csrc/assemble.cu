@@ -1036,7 +1036,8 @@ static int launch_group(int type, int tet_rule, const AsmParams& P, cudaStream_t
 int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
              double* b, cudaStream_t s) {
   if (!op || !m || !row_ptr || !node_map || !A || !b) return fail(FEA_ERR_ARG, "fea_assemble: null argument");
-  if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY && op->kind != FEA_OP_J2)
+  if (op->kind != FEA_OP_DIFFUSION && op->kind != FEA_OP_ELASTICITY && op->kind != FEA_OP_J2 &&
+      op->kind != FEA_OP_NEOHOOKE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown operator kind");
   if (op->precision != FEA_FP64 && op->precision != FEA_FP32_INTEGRATE && op->precision != FEA_FP32_ADAPTIVE)
     return fail(FEA_ERR_ARG, "fea_assemble: unknown precision");
@@ -1050,7 +1051,8 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     return fail(FEA_ERR_ARG, "fea_assemble: build the pattern and map for ndof = " + std::to_string(D) + " first");
   if (op->scatter == FEA_SCATTER_MULTIDEP) {
     // its own persistent launch over the subdomains (the schedule is not used)
-    if (op->kind == FEA_OP_J2) return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: FEA_SCATTER_MULTIDEP assembles diffusion and elasticity");
+    if (op->kind == FEA_OP_J2 || op->kind == FEA_OP_NEOHOOKE)
+      return fail(FEA_ERR_UNSUPPORTED, "fea_assemble: FEA_SCATTER_MULTIDEP assembles diffusion and elasticity");
     if (op->kind == FEA_OP_ELASTICITY && !(op->poisson > -1.0 && op->poisson < 0.5))
       return fail(FEA_ERR_ARG, "fea_assemble: poisson must be in (-1, 0.5)");
     if (op->chunk < 0 || op->n_ctas < 0 || op->lock_timeout_us < 0)
@@ -1069,6 +1071,7 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     for (int k = 2; k < nev; ++k) FEA_CUDA(cudaEventRecord(ev[k], s));
     return FEA_OK;
   }
+  if (op->kind == FEA_OP_NEOHOOKE) return assemble_nh(op, m, row_ptr, node_map, A, b, s);
   if (op->schedule != FEA_SCHED_PER_TYPE) return assemble_persistent(op, m, row_ptr, node_map, A, b, s);
   if (op->kind == FEA_OP_J2) return assemble_j2(op, m, row_ptr, node_map, A, b, s);
   if (op->kind == FEA_OP_ELASTICITY) {

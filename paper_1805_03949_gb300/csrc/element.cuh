@@ -183,6 +183,20 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float(((hi & 0x80000000u) | ((uint32_t)E << 23) | kept) + up);
 }
 
+// an FP64 value in the tile precision: exact for FP64 tiles, rounded to
+// nearest even by integer instructions for FP32 tiles (keeps the FP64 pipe,
+// which also runs the hardware conversion, free for the arithmetic)
+template <typename R>
+__device__ __forceinline__ R to_tile(double x);
+template <>
+__device__ __forceinline__ double to_tile<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float to_tile<float>(double x) {
+  return f64_to_f32_rn(x);
+}
+
 __device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {
   C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
   C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];

@@ -160,6 +160,8 @@ int assemble_persistent(const fea_operator* op, fea_mesh* m, const int64_t* row_
                         double* A, double* b, cudaStream_t s);
 int assemble_j2(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
                 double* b, cudaStream_t s);
+int assemble_nh(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map, double* A,
+                double* b, cudaStream_t s);
 int launch_persistent_batch(const fea_operator* op, const void* tab, const int32_t* tab_slot, const SchedArgs& S,
                             int n_ctas, bool dry, cudaStream_t s, int* grid_out);
 size_t batch_entry_bytes();

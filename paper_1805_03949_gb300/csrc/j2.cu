@@ -216,17 +216,18 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
     for (int i = 0; i < 6; ++i) P.stress_out[slot * 6 + i] = r.sig[i];
   }
   const double W = rr.w[q] * det * (1.0 / (s * s * s));
-  sm.C[le][q][0] = (R)W;
-  sm.C[le][q][1] = (R)(W * (P.kappa - 2.0 * P.mu * r.theta / 3.0));
-  sm.C[le][q][2] = (R)(W * P.mu * r.theta);
-  sm.C[le][q][3] = (R)(W * 2.0 * P.mu * r.theta_bar);
+  sm.C[le][q][0] = to_tile<R>(W);
+  sm.C[le][q][1] = to_tile<R>(W * (P.kappa - 2.0 * P.mu * r.theta / 3.0));
+  sm.C[le][q][2] = to_tile<R>(W * P.mu * r.theta);
+  sm.C[le][q][3] = to_tile<R>(W * 2.0 * P.mu * r.theta_bar);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) sm.S[le][q][k] = (R)(W * r.sig[k]);
+  for (int k = 0; k < 6; ++k) sm.S[le][q][k] = to_tile<R>(W * r.sig[k]);
   // h_a = n g_a in the tile precision (n = 0 at elastic points)
-  const R n0 = (R)r.n[0], n1 = (R)r.n[1], n2 = (R)r.n[2], n3 = (R)r.n[3], n4 = (R)r.n[4], n5 = (R)r.n[5];
+  const R n0 = to_tile<R>(r.n[0]), n1 = to_tile<R>(r.n[1]), n2 = to_tile<R>(r.n[2]), n3 = to_tile<R>(r.n[3]),
+          n4 = to_tile<R>(r.n[4]), n5 = to_tile<R>(r.n[5]);
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
-    const R g0 = (R)gd[a][0], g1 = (R)gd[a][1], g2 = (R)gd[a][2];
+    const R g0 = to_tile<R>(gd[a][0]), g1 = to_tile<R>(gd[a][1]), g2 = to_tile<R>(gd[a][2]);
     sm.G[le][q][a][0] = g0;
     sm.G[le][q][a][1] = g1;
     sm.G[le][q][a][2] = g2;

@@ -29,7 +29,7 @@ FEA_ERR_INDEX_OVERFLOW = -7
 FEA_ERR_UNSUPPORTED = -8
 
 FEA_TET4, FEA_PYR5, FEA_PRISM6, FEA_HEX8 = 0, 1, 2, 3
-FEA_OP_DIFFUSION, FEA_OP_ELASTICITY, FEA_OP_J2 = 0, 1, 2
+FEA_OP_DIFFUSION, FEA_OP_ELASTICITY, FEA_OP_J2, FEA_OP_NEOHOOKE = 0, 1, 2, 3
 FEA_SCHED_PER_TYPE, FEA_SCHED_STEAL, FEA_SCHED_QUEUES, FEA_SCHED_QUEUES_STEAL = 0, 1, 2, 3
 FEA_FP64, FEA_FP32_INTEGRATE, FEA_FP32_ADAPTIVE = 0, 1, 2
 FEA_SCATTER_ATOMIC, FEA_SCATTER_COLOR, FEA_SCATTER_BLOCK, FEA_SCATTER_ROWS, FEA_SCATTER_MULTIDEP = 0, 1, 2, 3, 4
@@ -67,7 +67,8 @@ class fea_operator(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("reserved3", ctypes.c_int32),
                 ("u_d", ctypes.c_void_p), ("state_in_d", ctypes.c_void_p), ("state_out_d", ctypes.c_void_p),
                 ("yield_out_d", ctypes.c_void_p), ("iters_out_d", ctypes.c_void_p),
-                ("lock_timeout_us", ctypes.c_int32), ("reserved4", ctypes.c_int32), ("span_d", ctypes.c_void_p)]
+                ("lock_timeout_us", ctypes.c_int32), ("reserved4", ctypes.c_int32), ("span_d", ctypes.c_void_p),
+                ("mass", ctypes.c_double)]
 
 
 def _load():
@@ -457,7 +458,7 @@ def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER
                   schedule=FEA_SCHED_PER_TYPE, chunk=0, n_ctas=0, queue=None, queue_off=None, item_ns=None,
                   item_cta=None, sigma0=1e-3, sigma_inf=3e-3, delta=300.0, hardening=1e-2, tol_g=1e-13,
                   tol_step=1e-15, max_iter=12, u=None, state_in=None, state_out=None, yield_out=None,
-                  iters_out=None, lock_timeout_us=0, span=None) -> fea_operator:
+                  iters_out=None, lock_timeout_us=0, span=None, mass=0.0) -> fea_operator:
     """Operator struct; tensors (device) are referenced by pointer, the caller keeps them alive."""
     op = fea_operator()
     op.kind, op.precision, op.scatter, op.tet_rule = kind, precision, scatter, tet_rule
@@ -473,6 +474,7 @@ def make_operator(kind=FEA_OP_DIFFUSION, precision=FEA_FP64, scatter=FEA_SCATTER
     op.u_d, op.state_in_d, op.state_out_d = _dptr(u), _dptr(state_in), _dptr(state_out)
     op.yield_out_d, op.iters_out_d = _dptr(yield_out), _dptr(iters_out)
     op.lock_timeout_us, op.span_d = lock_timeout_us, _dptr(span)
+    op.mass = mass
     return op
 
 
