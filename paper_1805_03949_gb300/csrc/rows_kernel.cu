@@ -350,16 +350,18 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 // CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
 // shared-memory stages.  Warps 0-5 (producers) fill stage i & 1 for block i:
 // the task lists by TMA bulk copy, the row starts, and the FP64-geometry
-// records of the block's elements; warps 6-13 (consumers) run the tasks of
+// records of the block's elements; warps 6-15 (consumers) run the tasks of
 // block i - 1 meanwhile.  The stages are handed over by mbarriers: full[s]
-// (1 arrival with the copy bytes + 192 producer arrivals) and empty[s] (256
-// consumer arrivals).  Six producer warps keep up with eight consumer warps on
-// a hex mesh (measured: 4 producer warps leave the consumers waiting, 8 cost
-// registers).  Every wait is bounded; a timeout latches
-// FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
+// (1 arrival with the copy bytes + 192 producer arrivals) and empty[s] (320
+// consumer arrivals).  The consumers bound the kernel (alone they take 90 %
+// of its time, the producers 65 %), so they get the ten warps; six producer
+// warps keep up with them (measured per 128^3 step: 6 + 8 warps 5.79 ms,
+// 6 + 10 5.48, 6 + 12 5.95 (register cap), 4 + 12 6.14, 7 + 9 5.90).  Every
+// wait is bounded; a timeout latches FEA_ERR_TIMEOUT, and the copies in
+// flight are waited for before exit.
 // ---------------------------------------------------------------------------
 constexpr int kPipeProducers = 192;
-constexpr int kPipeConsumers = 256;
+constexpr int kPipeConsumers = 320;
 
 template <int OP>
 __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
