@@ -1,0 +1,44 @@
+"""The reference arm of bench.py (the oracle timed on the host cores) runs on
+CPU and prints one JSON line carrying the same metric and workload name as
+the GPU arm, for one process and for two ranks (only rank 0 prints)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(extra_env=None, n=8):
+    env = dict(os.environ, **(extra_env or {}))
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--n", str(n), "--ref-layers", "1"],
+                         capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_prints_one_line_with_the_workload_name():
+    import bench
+    lines = _run()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "elements/s" and d["higher_is_better"] is True
+    assert d["metric"] == bench.METRIC
+    assert d["config"]["workload"] == bench.c2_workload_name(8)
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_workload_name_counts_the_lattice_nonzeros():
+    """9 (3n + 1)^3 is the nonzero count of the oracle's own pattern."""
+    import bench
+    from oracle import oracle
+    from paper_1805_03949_gb300 import meshgen as mg
+    for n in (1, 2, 5):
+        rp, cols, _ = oracle.pattern(mg.hex_cube(n, 0.2, 2), 3)
+        assert f"{len(cols):,} nonzeros" in bench.c2_workload_name(n)
+
+
+def test_other_ranks_print_nothing():
+    assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
