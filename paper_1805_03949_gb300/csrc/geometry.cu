@@ -11,9 +11,10 @@
 // and its right-hand side b^e_a = sum_q W(q) N_a(q) f.
 //
 // FEA_FP32_INTEGRATE: J, its cofactors C and det J in FP64 for every element
-// (node coordinates relative to node 0; the trilinear hex in modal form, see
-// hex8_modal); C and det J are rounded to FP32 once and the gradients formed
-// from them in FP32.
+// (the trilinear hex in modal form from its absolute corner coordinates, see
+// hex8_modal -- the modal transform differences them exactly in FP64; other
+// types from coordinates relative to node 0); C and det J are rounded to FP32
+// once and the gradients formed from them in FP32.
 // FEA_FP32_ADAPTIVE: coordinates relative to node 0 are subtracted in FP64 and
 // rounded to FP32 once per (element, node); J, det J and J^{-1} are FP32 unless
 // the element is distorted (Frobenius condition number of J above
