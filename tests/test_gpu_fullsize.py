@@ -82,7 +82,7 @@ def test_c2_pattern_closed_form(c2):
                 assert col[rp[3 * i] + 3 * nmap[e, a, bb]] == 3 * conn[e, bb]
 
 
-@pytest.mark.parametrize("scatter", [3, 0, 1, 2])
+@pytest.mark.parametrize("scatter", [3, 0, 1, 2, 4])
 @pytest.mark.parametrize("precision", [1, 0])
 def test_c2_sampled_rows(oracle, c2, precision, scatter):
     fea, mesh, s = c2
@@ -116,3 +116,72 @@ def test_c3_hybrid_sampled_rows(oracle):
             assert abs(float(s.b.sum()) - 1.0) < (1e-9 if precision == 0 else 1e-6)
     finally:
         s.close()
+
+
+def test_c2_product_sampled_rows(c2):
+    """y = A x on the full system, in the bench's call: sampled rows recomputed
+    on the CPU from the same A and the column indices."""
+    import torch
+    fea, mesh, s = c2
+    s.assemble(fea.make_operator(kind=1, precision=0, young=1.0, poisson=0.3))
+    x = torch.randn(s.b.numel(), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    y = torch.full_like(x, float("nan"))
+    fea.fea_spmv(s.handle, 3, s.row_ptr, s.A, x, y)
+    s.check()
+    assert not torch.isnan(y).any()
+    rp = s.row_ptr.cpu().numpy()
+    rows = np.concatenate([3 * _sample_nodes(128, np.random.default_rng(12)) + c for c in range(3)])
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    for r in rows:
+        lo, hi = rp[r], rp[r + 1]
+        a = s.A[lo:hi].cpu().numpy()
+        cols = s.col_idx[lo:hi].cpu().numpy()
+        ref = float(np.dot(a, xh[cols]))
+        assert abs(yh[r] - ref) <= 1e-13 * np.abs(a).sum() * np.abs(xh).max(), r
+
+
+def _nh_rows(oracle, mesh, U, nodes, **kw):
+    """All rows of the requested nodes of the finite-strain Jacobian and
+    internal force, summed over the elements holding each node."""
+    conn = mesh.conn.reshape(-1, 8)
+    out = []
+    for node in nodes:
+        rows = {}
+        b = np.zeros(3); sb = np.zeros(3)
+        for e, a in zip(*np.nonzero(conn == node)):
+            r = oracle.nh_element(3, mesh.coords[conn[e]], U[conn[e]], **kw)
+            for bb in range(8):
+                j = int(conn[e, bb])
+                v, nv = rows.get(j, (np.zeros((3, 3)), np.zeros((3, 3))))
+                rows[j] = (v + r["A"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3], nv + r["NA"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3])
+            b += r["b"][3 * a:3 * a + 3]
+            sb += r["Nb"][3 * a:3 * a + 3]
+        out.append((rows, b, sb))
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_c2_finite_strain_sampled_rows(oracle, c2, precision):
+    import torch
+    fea, mesh, s = c2
+    U = mg.fourier_displacement(mesh.coords, 0.004, seed=6) + 0.05 * mesh.coords[:, [1, 2, 0]]
+    u = torch.tensor(U.reshape(-1), device="cuda")
+    s.A.fill_(float("nan"))
+    s.assemble(fea.make_operator(kind=fea.FEA_OP_NEOHOOKE, precision=precision, u=u, young=1.0, poisson=0.3))
+    s.check()
+    tol = FP64_TOL if precision == 0 else FP32_TOL
+    nodes = _sample_nodes(128, np.random.default_rng(13), count=12)
+    rp = s.row_ptr.cpu().numpy()
+    worst = 0.0
+    for node, (rows, b, sb) in zip(nodes, _nh_rows(oracle, mesh, U, nodes)):
+        for c in range(3):
+            lo, hi = rp[3 * node + c], rp[3 * node + c + 1]
+            A = s.A[lo:hi].cpu().numpy()
+            cols = s.col_idx[lo:hi].cpu().numpy()
+            assert hi - lo == 3 * len(rows)
+            for k in range(0, hi - lo, 3):
+                j = int(cols[k]) // 3
+                v, nv = rows[j]
+                worst = max(worst, float(np.max(np.abs(A[k:k + 3] - v[c]) / nv[c])))
+            worst = max(worst, abs(float(s.b[3 * node + c]) - b[c]) / sb[c])
+    assert worst <= tol, worst
