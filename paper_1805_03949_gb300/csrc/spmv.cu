@@ -24,8 +24,9 @@ namespace fea {
 
 // On GB300 this product is bound by the FP64 pipe (two DFMA per SM and clock)
 // about as tightly as by HBM: per 8-byte value of A, one DFMA takes 1.6 ps of
-// the GPU's FP64 rate and its bytes 1.2 ps of the HBM copy rate.  So the kernel spends FP64 work on the nnz
-// multiply-adds and almost nothing else: two lanes per scalar row, lane `sub`
+// the GPU's FP64 rate and its bytes 1.2 ps of the HBM copy rate.  So the
+// kernel spends FP64 work on the nnz multiply-adds and almost nothing else:
+// two lanes per scalar row, lane `sub`
 // taking the values t = sub, sub + 2, ... of the row (neighbouring lanes read
 // neighbouring values of A, the other half of each sector is the next
 // instruction's L1 hit), one shuffle level to finish the row.  No shared
