@@ -52,6 +52,12 @@ def test_host_side_argument_checks(clib):
     assert clib.fea_mesh_info(None, ctypes.byref(n), None, None) == -1
     assert clib.fea_assemble(None, None, None, None, None, None, None) == -1
     assert clib.fea_check(None, None) == -1
+    # the product, the multidependence plan and its test hook reject a null mesh
+    assert clib.fea_spmv(None, 3, None, None, None, None, None, None, None) == -1
+    info = (ctypes.c_int64 * 4)()
+    assert clib.fea_multidep_plan(None, 0, info, None, None, None, None) == -1
+    assert clib.fea_multidep_hold(None, 0, 1) == -1
+    assert b"multidep" in clib.fea_last_error()
 
 
 def test_binding_structs_match_the_header(tmp_path):
