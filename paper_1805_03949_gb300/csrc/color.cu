@@ -2,14 +2,19 @@
 //
 // Alg. "coloring" of the MPI+X assembly paper (Sec. 3.2.1): elements are
 // colored so that no two elements of one color share a node; each color is
-// then assembled without atomics.  The coloring is built once per mesh on the
-// GPU by Luby / Jones-Plassmann rounds: in round r every still-uncolored
-// element whose (hashed, seeded) priority beats all its uncolored neighbours
-// (elements sharing a node) takes color r.  Each round colors an independent
-// set, so the result is a valid coloring by construction; the test-suite
-// checks it anyway.  The element lists of each (color, type) pair keep the
-// input order, which preserves what spatial locality a color class has (the
-// paper notes that coloring loses most of it).
+// then assembled without atomics.  The coloring is built once per mesh:
+// greedy first-fit on the host, in element order -- an element takes the
+// lowest color that no element sharing one of its nodes holds yet (a 64-bit
+// mask of the colors at every node) -- which gives the 8 colors of a
+// structured hex mesh and few more elsewhere; fewer colors mean fewer and
+// larger launches.  A mesh that would need more than 64 colors is colored on
+// the GPU by Luby / Jones-Plassmann rounds instead: in round r every
+// still-uncolored element whose (hashed, seeded) priority beats all its
+// uncolored neighbours takes color r.  Both give a valid coloring by
+// construction; the test-suite checks it anyway.  The element lists of each
+// (color, type) pair keep the input order, which preserves what spatial
+// locality a color class has (the paper notes that coloring loses most of
+// it).
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -48,7 +53,27 @@ __global__ void k_color_round(int round, int64_t n_elems, const int64_t* conn_of
   atomicAdd(left, 1ull);
 }
 
-int build_color_plan(fea_mesh* m, cudaStream_t s) {
+// Greedy first-fit in element order (host).  Returns false when an element
+// would need a 65th color.
+static bool greedy_colors(int64_t E, int64_t N, const std::vector<int64_t>& off, const std::vector<int32_t>& conn,
+                          std::vector<int32_t>& color, int* n_colors) {
+  std::vector<uint64_t> mask(N, 0);
+  int nc = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t used = 0;
+    for (int64_t u = off[e]; u < off[e + 1]; ++u) used |= mask[conn[u]];
+    if (used == ~0ull) return false;
+    const int c = __builtin_ctzll(~used);
+    color[e] = c;
+    nc = std::max(nc, c + 1);
+    for (int64_t u = off[e]; u < off[e + 1]; ++u) mask[conn[u]] |= 1ull << c;
+  }
+  *n_colors = nc;
+  return true;
+}
+
+// Luby / Jones-Plassmann rounds on the GPU; *rounds = colors used.
+static int jp_colors(fea_mesh* m, cudaStream_t s, std::vector<int32_t>& hc, int* rounds_out) {
   const int64_t E = m->n_elems;
   int32_t* color = nullptr;
   unsigned long long* done = nullptr;
@@ -71,12 +96,27 @@ int build_color_plan(fea_mesh* m, cudaStream_t s) {
     cudaFree(done);
     return fail(FEA_ERR_UNSUPPORTED, "coloring did not finish within " + std::to_string(kMaxRounds) + " rounds");
   }
-  std::vector<int32_t> hc(E);
-  std::vector<int64_t> off(E + 1);
+  hc.resize(E);
   FEA_CUDA(cudaMemcpy(hc.data(), color, E * sizeof(int32_t), cudaMemcpyDeviceToHost));
-  FEA_CUDA(cudaMemcpy(off.data(), m->conn_off, (E + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
   cudaFree(color);
   cudaFree(done);
+  *rounds_out = rounds;
+  return FEA_OK;
+}
+
+int build_color_plan(fea_mesh* m, cudaStream_t s) {
+  const int64_t E = m->n_elems;
+  std::vector<int64_t> off(E + 1);
+  std::vector<int32_t> conn(m->conn_len);
+  FEA_CUDA(cudaMemcpyAsync(off.data(), m->conn_off, (E + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FEA_CUDA(cudaMemcpyAsync(conn.data(), m->conn, m->conn_len * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FEA_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> hc(E);
+  int rounds = 0;
+  if (!greedy_colors(E, m->n_nodes, off, conn, hc, &rounds)) {
+    int rc = jp_colors(m, s, hc, &rounds);
+    if (rc) return rc;
+  }
   // (color, type) segments of group-local indices, input order inside each
   ColorPlan* P = new ColorPlan();
   P->n_colors = rounds;
