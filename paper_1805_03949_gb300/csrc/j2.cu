@@ -154,9 +154,15 @@ __device__ __forceinline__ void j2_return(const J2Params& P, const double eps[6]
 
 // Phase 1 of point q of element le: FP64 geometry, strain and return map;
 // writes the per-point factors of the tile precision into shared memory.
-template <class Cfg>
+// J' = s J is the reference Jacobian scaled by a power of two.  MODAL (hex8,
+// FP32 tiles): Ju' = s Ju is the displacement field's reference Jacobian from
+// the modal transform of the nodal displacements, and the displacement
+// gradient is Ju J^-1 = Ju' C'^T / det' in FP64 (27 + 9 operations), so the
+// shape-function gradients are only needed in the tile precision: formed in
+// FP32 from C' and det' rounded once each, as the elasticity tile forms them.
+template <class Cfg, bool MODAL = false>
 __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& rr, const J2Params& P, int le, int q,
-                                         int64_t et, double (&J)[3][3], double s) {
+                                         int64_t et, double (&J)[3][3], double s, const double (*Ju)[3] = nullptr) {
   using R = typename Cfg::R;
   constexpr int NN = Cfg::NN;
   const int64_t g = j2_group_index(P, et);
@@ -176,19 +182,43 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
       for (int i = 0; i < 3; ++i) sm.G[le][q][a][i] = sm.H[le][q][a][i] = R(0);
     return;
   }
-  const double inv = s / det;
-  // gradients (FP64) and the displacement gradient H_ij = sum_a u_a,i g_a,j
-  double gd[NN][3];
+  // the displacement gradient H_ij = sum_a u_a,i g_a,j (FP64) and the
+  // gradients g_a in the tile precision
   double Hu[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-  for (int a = 0; a < NN; ++a) {
+  R gt[NN][3];
+  if constexpr (MODAL) {
+    static_assert(!std::is_same<R, double>::value, "the modal strain path forms FP32 gradients");
+    const double rdet = 1.0 / det;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      gd[a][i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Hu[i][j] = (Ju[i][0] * C[j][0] + Ju[i][1] * C[j][1] + Ju[i][2] * C[j][2]) * rdet;
+    float Cf[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Hu[i][j] = fma(sm.U[le][a][i], gd[a][j], Hu[i][j]);
+      for (int j = 0; j < 3; ++j) Cf[i][j] = f64_to_f32_rn(C[i][j]);
+    const float invf = (float)s / f64_to_f32_rn(det);
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        gt[a][i] = (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * invf;
+  } else {
+    const double inv = s / det;
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      double gd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        gd[i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Hu[i][j] = fma(sm.U[le][a][i], gd[j], Hu[i][j]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gt[a][i] = to_tile<R>(gd[i]);
+    }
   }
   const double eps[6] = {Hu[0][0], Hu[1][1], Hu[2][2], 0.5 * (Hu[0][1] + Hu[1][0]), 0.5 * (Hu[1][2] + Hu[2][1]),
                          0.5 * (Hu[0][2] + Hu[2][0])};
@@ -227,7 +257,7 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
           n4 = to_tile<R>(r.n[4]), n5 = to_tile<R>(r.n[5]);
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
-    const R g0 = to_tile<R>(gd[a][0]), g1 = to_tile<R>(gd[a][1]), g2 = to_tile<R>(gd[a][2]);
+    const R g0 = gt[a][0], g1 = gt[a][1], g2 = gt[a][2];
     sm.G[le][q][a][0] = g0;
     sm.G[le][q][a][1] = g1;
     sm.G[le][q][a][2] = g2;
@@ -268,18 +298,34 @@ __device__ __forceinline__ void j2_tile_body(typename J2Cfg<TYPE, SLOT, PREC, SP
       const int64_t et = e0 + le;
       const bool valid = et < n_end;
       const int a = hex8_corner_node(p);
-      double v[3];
+      // FP32 tiles take the displacements to modal form as well (the strain
+      // then needs no FP64 gradients); sm.U holds modal coefficients after
+      constexpr bool kModalU = PREC != FEA_FP64;
+      double v[3], vu[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] : 0.0;
+      for (int i = 0; i < 3; ++i) {
+        v[i] = valid ? sm.X[le][a][i] : 0.0;
+        vu[i] = valid ? sm.U[le][a][i] : 0.0;
+      }
       hex8_modal(v);
+      if constexpr (kModalU) hex8_modal(vu);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < 3; ++i) sm.X[le][p][i] = v[i];
+      for (int i = 0; i < 3; ++i) {
+        sm.X[le][p][i] = v[i];
+        if constexpr (kModalU) sm.U[le][p][i] = vu[i];
+      }
       __syncwarp();
       if (valid) {
         double J[3][3];
         hex8_jacobian(sm.X[le], p, J);
-        j2_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
+        if constexpr (kModalU) {
+          double Ju[3][3];
+          hex8_jacobian(sm.U[le], p, Ju);
+          j2_point<Cfg, true>(sm, rr, P, le, p, et, J, 8.0, Ju);
+        } else {
+          j2_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
+        }
       }
     }
   } else {

@@ -72,10 +72,13 @@ __device__ __forceinline__ int64_t nh_group_index(const NHParams& P, int64_t et)
 
 // Phase 1 of point q of element le (FP64): J' = s J0 is the reference
 // Jacobian scaled by a power of two s; writes the point's factors in the
-// tile precision into shared memory.
-template <class Cfg>
+// tile precision into shared memory.  MODAL (hex8, FP32 tiles): Ju' = s Ju
+// is the displacement field's reference Jacobian from the modal transform of
+// the nodal displacements, so F - I = Ju' C'^T / det' in FP64 and the
+// reference gradients are formed in FP32 from C' and det' rounded once.
+template <class Cfg, bool MODAL = false>
 __device__ __forceinline__ void nh_point(typename Cfg::Smem& sm, const RefRule& rr, const NHParams& P, int le, int q,
-                                         int64_t et, double (&J)[3][3], double s) {
+                                         int64_t et, double (&J)[3][3], double s, const double (*Ju)[3] = nullptr) {
   using R = typename Cfg::R;
   constexpr int NN = Cfg::NN;
   const int64_t g = nh_group_index(P, et);
@@ -83,20 +86,43 @@ __device__ __forceinline__ void nh_point(typename Cfg::Smem& sm, const RefRule& 
   double C[3][3];
   cofactors(J, C);
   const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-  double gd[NN][3];
+  R gt[NN][3];  // g_a in the tile precision
   double F[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   double Fc[3][3], detF = 0.0;
   if (det > 0.0) {
-    const double inv = s / det;
-#pragma unroll
-    for (int a = 0; a < NN; ++a) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        gd[a][i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+    if constexpr (MODAL) {
+      static_assert(!std::is_same<R, double>::value, "the modal path forms FP32 gradients");
+      const double rdet = 1.0 / det;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) F[i][j] = fma(sm.U[le][a][i], gd[a][j], F[i][j]);
+        for (int j = 0; j < 3; ++j) F[i][j] += (Ju[i][0] * C[j][0] + Ju[i][1] * C[j][1] + Ju[i][2] * C[j][2]) * rdet;
+      float Cf[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Cf[i][j] = f64_to_f32_rn(C[i][j]);
+      const float invf = (float)s / f64_to_f32_rn(det);
+#pragma unroll
+      for (int a = 0; a < NN; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          gt[a][i] = (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * invf;
+    } else {
+      const double inv = s / det;
+#pragma unroll
+      for (int a = 0; a < NN; ++a) {
+        double gd[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          gd[i] = (rr.dN[q][a][0] * C[i][0] + rr.dN[q][a][1] * C[i][1] + rr.dN[q][a][2] * C[i][2]) * inv;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) F[i][j] = fma(sm.U[le][a][i], gd[j], F[i][j]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gt[a][i] = to_tile<R>(gd[i]);
+      }
     }
     cofactors(F, Fc);  // cof F = det F * F^-T
     detF = F[0][0] * Fc[0][0] + F[0][1] * Fc[0][1] + F[0][2] * Fc[0][2];
@@ -139,7 +165,7 @@ __device__ __forceinline__ void nh_point(typename Cfg::Smem& sm, const RefRule& 
     for (int j = 0; j < 3; ++j) Ft[i][j] = to_tile<R>(Fit[i][j]);
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
-    const R g0 = to_tile<R>(gd[a][0]), g1 = to_tile<R>(gd[a][1]), g2 = to_tile<R>(gd[a][2]);
+    const R g0 = gt[a][0], g1 = gt[a][1], g2 = gt[a][2];
     sm.G[le][q][a][0] = g0;
     sm.G[le][q][a][1] = g1;
     sm.G[le][q][a][2] = g2;
@@ -178,18 +204,34 @@ __device__ __forceinline__ void nh_tile_body(typename NHCfg<TYPE, SLOT, PREC, SP
       const int64_t et = e0 + le;
       const bool valid = et < n_end;
       const int a = hex8_corner_node(p);
-      double v[3];
+      // FP32 tiles take the displacements to modal form as well (F then
+      // needs no FP64 gradients); sm.U holds modal coefficients after
+      constexpr bool kModalU = PREC != FEA_FP64;
+      double v[3], vu[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) v[i] = valid ? sm.X[le][a][i] : 0.0;
+      for (int i = 0; i < 3; ++i) {
+        v[i] = valid ? sm.X[le][a][i] : 0.0;
+        vu[i] = valid ? sm.U[le][a][i] : 0.0;
+      }
       hex8_modal(v);
+      if constexpr (kModalU) hex8_modal(vu);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < 3; ++i) sm.X[le][p][i] = v[i];
+      for (int i = 0; i < 3; ++i) {
+        sm.X[le][p][i] = v[i];
+        if constexpr (kModalU) sm.U[le][p][i] = vu[i];
+      }
       __syncwarp();
       if (valid) {
         double J[3][3];
         hex8_jacobian(sm.X[le], p, J);
-        nh_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
+        if constexpr (kModalU) {
+          double Ju[3][3];
+          hex8_jacobian(sm.U[le], p, Ju);
+          nh_point<Cfg, true>(sm, rr, P, le, p, et, J, 8.0, Ju);
+        } else {
+          nh_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
+        }
       }
     }
   } else {
