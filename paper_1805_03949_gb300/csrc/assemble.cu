@@ -212,14 +212,11 @@ struct TileSmem {
 // det J = det'/s^3, grad N_a = J^{-T} grad_xi N_a = s C' grad_xi N_a / det'.
 // FP64 tiles keep FP64; FP32 tiles round the cofactors and the determinant
 // once and form the gradients in FP32.
+// (the point's values from the cofactors C' and det' of J' = s J)
 template <int OP, int NN, typename Smem>
-__device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
-                                                double (&J)[3][3], double s, double xq, const AsmParams& P) {
+__device__ __forceinline__ void geometry_store(Smem& sm, const RefRule& rr, int le, int q, const double (&C)[3][3],
+                                               double det, double s, double xq, const AsmParams& P) {
   using R = std::remove_reference_t<decltype(sm.G[0][0][0][0])>;
-  double C[3][3];
-  cofactors(J, C);
-  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-  if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
   if constexpr (std::is_same<R, double>::value) {
     const double wd = rr.w[q] * det * (1.0 / (s * s * s));
     const double inv = s / det;
@@ -256,6 +253,16 @@ __device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int
       sm.S[le][q] = wdf;
     }
   }
+}
+
+template <int OP, int NN, typename Smem>
+__device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
+                                                double (&J)[3][3], double s, double xq, const AsmParams& P) {
+  double C[3][3];
+  cofactors(J, C);
+  const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)elem_id);
+  geometry_store<OP, NN>(sm, rr, le, q, C, det, s, xq, P);
 }
 
 // FP64 geometry of point q of element le, J from the node coordinates
@@ -400,6 +407,40 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
             xq = 0.125 * acc;
           }
           geometry_finish<OP, NN>(sm, rr, le, p, original_id(P, et), J, 8.0, xq, P);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  if constexpr (NN == 4) {  // tet4
+    if (all64) {
+      // a linear tet has one Jacobian (its shape-function derivatives are the
+      // same at every point): J, its cofactors and det J once per element,
+      // then each point's values from them
+      for (int le = threadIdx.x; le < EPC; le += Cfg::THREADS) {
+        const int64_t et = e0 + le;
+        if (et >= n_end) continue;
+        double d[NN][3], J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+        for (int a = 1; a < NN; ++a) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) d[a][i] = sm.X[le][a][i] - sm.X[le][0][i];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) J[i][j] += d[a][i] * rr.dN[0][a][j];
+        }
+        double C[3][3];
+        cofactors(J, C);
+        const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+        if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)original_id(P, et));
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          double xq = sm.X[le][0][0];
+#pragma unroll
+          for (int a = 1; a < NN; ++a) xq += rr.N[q][a] * d[a][0];
+          geometry_store<OP, NN>(sm, rr, le, q, C, det, 1.0, xq, P);
         }
       }
       __syncthreads();
