@@ -203,3 +203,44 @@ def test_coloring_is_valid(name):
         assert fea.fea_assemble_launches(fea.make_operator(kind=kind, scatter=1), s.handle) >= n_colors
     finally:
         s.close()
+
+
+def _tet_fan(count=70):
+    """`count` tets sharing node 0 (and no other node): every element touches
+    every other, so any valid coloring needs `count` colors."""
+    rng = np.random.default_rng(9)
+    coords = [np.zeros(3)]
+    conn = []
+    for k in range(count):
+        d = np.array([np.cos(2 * np.pi * k / count), np.sin(2 * np.pi * k / count), 0.3 * k / count])
+        base = len(coords)
+        pts = [d, d + np.array([0.1, 0.0, 0.0]) + 0.01 * rng.random(3), d + np.array([0.0, 0.1, 0.1])]
+        a = np.array(pts)
+        if np.linalg.det(a) < 0:                      # orient every tet positively
+            pts[1], pts[2] = pts[2], pts[1]
+        coords += pts
+        conn += [0, base, base + 1, base + 2]
+    coords = np.array(coords)
+    return mg.Mesh(coords=coords, types=np.zeros(count, dtype=np.uint8),
+                   conn_offsets=np.arange(0, 4 * count + 1, 4, dtype=np.int64), conn=np.array(conn, dtype=np.int32))
+
+
+def test_coloring_beyond_64_colors_takes_the_device_rounds(oracle):
+    """Greedy coloring keeps a 64-bit mask per node; a mesh needing more colors
+    is colored by Luby / Jones-Plassmann rounds on the GPU instead.  The
+    coloring stays valid and the COLOR assembly matches the oracle."""
+    fea = engine()
+    mesh = _tet_fan(70)
+    s = fea.System.from_mesh(mesh, 1)
+    try:
+        s.assemble(fea.make_operator(kind=0, scatter=fea.FEA_SCATTER_COLOR, precision=0, tet_rule=1, k0=1.0,
+                                     k2=1.0, source=1.0))
+        s.check()
+        n_colors, colors = fea.fea_color_info(s.handle, mesh.n_elems)
+        assert n_colors >= 70 and len(np.unique(colors)) == 70     # one element per color
+        ref = oracle.assemble(mesh, 0, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
+        errA, zA = err_vs_oracle(s.A.cpu().numpy(), ref["A"], ref["NA"])
+        errb, zb = err_vs_oracle(s.b.cpu().numpy(), ref["b"], ref["Nb"])
+        assert max(errA, errb, zA, zb) <= FP64_TOL
+    finally:
+        s.close()
