@@ -416,7 +416,9 @@ typedef struct {
 } fea_batch_entry;
 
 /* op: FEA_OP_DIFFUSION or FEA_OP_ELASTICITY (schedule and scatter fields are
- * ignored: the batch always uses work stealing and the ATOMIC scatter);
+ * ignored: the batch always uses work stealing and the ATOMIC scatter; the
+ * items are listed mesh by mesh, fewest elements first, which minimises the
+ * mean per-mesh latency);
  * op->chunk (0 = 128) and op->n_ctas (0 = resident CTAs) give the initial
  * configuration.  1 <= n_meshes <= 32767.  Synchronous. */
 int fea_batch_create(const fea_operator* op, int n_meshes, const fea_batch_entry* entries_h, fea_batch** out);
