@@ -316,6 +316,7 @@ def run_ours(args, rank, world, local_rank):
     # read-back finished.
     op = variants[head]
     fea.set_events(op, None)
+    host_numa = _bind_host_to_gpu_numa(dev.index if dev.index is not None else 0)
     coords_h = torch.from_numpy(mesh.coords.reshape(-1)).pin_memory()
     coords_d = torch.empty_like(coords_h, device=dev)
     A_d = [sysm.A, torch.empty_like(sysm.A)]
@@ -432,7 +433,8 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "e2e": {"value": world * E / (e2e_ms * 1e-3), "unit": "elements/s",
                     "h2d_bytes_per_step": int(coords_h.numel() * 8),
-                    "d2h_bytes_per_step": int((A_h.numel() + b_h.numel()) * 8)},
+                    "d2h_bytes_per_step": int((A_h.numel() + b_h.numel()) * 8),
+                    "host_numa_node": host_numa},
             "gpu_launches": r["launches"] * r["steps"],
         }
         if not args.no_cpu_baseline:
@@ -451,6 +453,30 @@ def run_ours(args, rank, world, local_rank):
 # ---------------------------------------------------------------------------
 # the other workloads (one GPU, after the headline line's measurement)
 # ---------------------------------------------------------------------------
+
+def _bind_host_to_gpu_numa(device_index: int):
+    """Run this process on the CPUs of the GPU's NUMA node, so that the pinned
+    host buffers allocated next (first touch) sit next to the GPU's link.
+    Returns the node, or None when sysfs does not tell (nothing changes)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(device_index)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            if part:
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return node
+    except (AttributeError, OSError, ValueError):
+        return None
+
 
 def _time_calls(fn, steps, warmup=2):
     import torch
