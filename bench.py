@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -69,10 +70,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -221,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
         variants = {k: v for k, v in variants.items() if k in keep}
     plan_s = {}
     results = {}
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(local_rank, args.clocks_dir)
     clocks_started = False
     for name, op in variants.items():
         fea.set_events(op, None)
@@ -716,6 +717,8 @@ def main():
     ap.add_argument("--cpu-layers", type=int, default=8)
     ap.add_argument("--ref-layers", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="where the raw nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--configs", default="c3,c4,c5",
                     help="other workloads timed after the headline one (comma list of c3, c4, c5; '' for none)")
     args = ap.parse_args()
