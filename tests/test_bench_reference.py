@@ -42,3 +42,31 @@ def test_workload_name_counts_the_lattice_nonzeros():
 
 def test_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_fp64_accumulation_count_matches_brute_force():
+    """The roofline's FP64 accumulation adds: for every entry of the upper 3x3
+    blocks (i <= j) and of b, (contributions - 1), counted element by element
+    on small meshes against the closed form in the bench."""
+    import bench
+    import numpy as np
+    from paper_1805_03949_gb300 import meshgen as mg
+    for n, jit in ((1, 0.0), (3, 0.2), (4, 0.1)):
+        mesh = mg.hex_cube(n, jit, 2)
+        conn = mesh.conn.reshape(-1, 8)
+        contrib = {}
+        bcount = np.zeros(mesh.n_nodes, dtype=np.int64)
+        for e in conn:
+            for a in range(8):
+                bcount[e[a]] += 1
+                for b in range(8):
+                    i, j = int(e[a]), int(e[b])
+                    if i <= j:
+                        contrib[(i, j)] = contrib.get((i, j), 0) + 1
+        # every element adds into 36 upper blocks (8 diagonal, 28 pairs), each
+        # of 9 entries; an entry with c contributions takes c - 1 adds
+        adds_A = 9 * sum(c - 1 for c in contrib.values())
+        adds_b = 3 * int((bcount - 1).clip(min=0).sum())
+        nnz = 9 * (3 * n + 1) ** 3
+        fl = bench.algorithmic_flops_hex_elasticity(mesh.n_elems, mesh.n_nodes, nnz)
+        assert fl["fp64_accumulate"] == adds_A + adds_b, n
