@@ -447,25 +447,28 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
       return;
     }
   }
-  for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
-    const int le = t / NQ, q = t % NQ;
-    const int64_t et = e0 + le;
-    if (et >= n_end) continue;
-    if (all64) {
-      geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
-    } else {
-      if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
-    }
-  }
-  if (!all64) {
-    __syncthreads();
+  // FP64 hex (modal) and tet tiles have returned above
+  if constexpr (!(PREC == FEA_FP64 && (kModal || NN == 4))) {
     for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
       const int le = t / NQ, q = t % NQ;
       const int64_t et = e0 + le;
-      if (et < n_end && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
+      if (et >= n_end) continue;
+      if (all64) {
+        geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
+      } else {
+        if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
+      }
     }
+    if (!all64) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
+        const int le = t / NQ, q = t % NQ;
+        const int64_t et = e0 + le;
+        if (et < n_end && sm.flag[le]) geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // phase 2: row block (a, columns b0 .. b0+NB) of element le, and its RHS
