@@ -118,7 +118,7 @@ class ClockSampler:
 # workload and algorithmic counts
 # ---------------------------------------------------------------------------
 
-def c2_mesh(n=128):
+def hex_cube_mesh(n=128):
     from paper_1805_03949_gb300 import meshgen as mg
     return mg.hex_cube(n, 0.2, 2)
 
@@ -194,7 +194,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    mesh = c2_mesh(args.n)
+    mesh = hex_cube_mesh(args.n)
     t0 = time.perf_counter()
     sysm = fea.System.from_mesh(mesh, 3, device=dev, with_cols=True)
     torch.cuda.synchronize()
@@ -413,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None,
             "dtype": "f32 integrate + f64 accumulate" if "fp32" in head else "f64",
             "data": "synthetic (seeded jittered hex8 cube; the paper's meshes are not available)",
-            "config": {"workload": c2_workload_name(args.n),
+            "config": {"workload": workload_name(args.n),
                        "variant": head, "l2": "inputs larger than L2 (A alone is 4.1 GB)",
                        "parallelism": f"replicas x{world} (partial-row, no exchange)"},
             "roofline": roof,
@@ -440,10 +440,10 @@ def run_ours(args, rank, world, local_rank):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
-        if world == 1 and args.configs:
+        if world == 1 and args.workloads:
             sysm.close()
             torch.cuda.empty_cache()
-            line["configs"] = other_configs(args, dev)
+            line["workloads"] = other_workloads(args, dev)
         print(json.dumps(line), flush=True)
     sysm.close()
     if dist is not None:
@@ -531,7 +531,7 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, 
                  "gain_with_steal": out["gauss_points_queues_steal"] / out["mlp_queues_steal"] - 1.0}
 
 
-def config_hybrid(dev, steps=5):
+def workload_hybrid(dev, steps=5):
     """Hybrid tet/pyramid/prism/hex diffusion, k = 1 + x^2, degree-2 rules: per-type launches
     against one persistent launch over every type, scheduled by stealing or by packed queues."""
     from paper_1805_03949_gb300 import fea, meshgen as mg
@@ -556,7 +556,7 @@ def config_hybrid(dev, steps=5):
         s.close()
 
 
-def config_j2(dev, steps=5):
+def workload_j2(dev, steps=5):
     """Elastoplastic hex8 (J2 / Voce), 96^3, second load step from the committed first step: the
     plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules."""
     import torch
@@ -598,7 +598,7 @@ def config_j2(dev, steps=5):
         s.close()
 
 
-def config_batch(dev, steps=10):
+def workload_batch(dev, steps=10):
     """256 tet4/hex8 elasticity meshes (log-uniform 1e3..2e5 elements), one graph-captured
     persistent launch, autotuned chunk and grid; aggregate rate and per-mesh latency."""
     import torch
@@ -628,10 +628,10 @@ def config_batch(dev, steps=10):
             s.close()
 
 
-def other_configs(args, dev):
+def other_workloads(args, dev):
     out = {}
-    wanted = [c for c in args.configs.split(",") if c]
-    for key, fn in (("c3", config_hybrid), ("c4", config_j2), ("c5", config_batch)):
+    wanted = [c for c in args.workloads.split(",") if c]
+    for key, fn in (("hybrid", workload_hybrid), ("j2", workload_j2), ("batch", workload_batch)):
         if key in wanted:
             t0 = time.perf_counter()
             out[key] = fn(dev)
@@ -657,7 +657,7 @@ def _slab(mesh, layers, n):
 def cpu_baseline(args, mesh=None, layers=None):
     from oracle import oracle as O
     n = args.n
-    mesh = mesh if mesh is not None else c2_mesh(n)
+    mesh = mesh if mesh is not None else hex_cube_mesh(n)
     layers = layers or args.cpu_layers
     sub = _slab(mesh, layers, n)
     pat = O.pattern(sub, 3)
@@ -665,12 +665,12 @@ def cpu_baseline(args, mesh=None, layers=None):
     O.assemble(sub, O.OP_ELASTICITY, pat=pat, young=1.0, poisson=0.3)
     dt = time.perf_counter() - t0
     return {"value": sub.n_elems / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {layers} of 128 cell layers of the workload ({sub.n_elems} elements), "
+            "sample": f"first {layers} of {n} cell layers of the workload ({sub.n_elems} elements), "
                       f"single-thread FP64 oracle, element-index order, pattern excluded",
             "seconds": dt}
 
 
-def c2_workload_name(n: int) -> str:
+def workload_name(n: int) -> str:
     """The bench workload, named by what it is (both arms use this name).  The
     scalar system of an n^3 hex lattice with 3 dofs per node has
     9 (3 n + 1)^3 nonzeros: per axis a node couples with itself and its two
@@ -682,7 +682,7 @@ def c2_workload_name(n: int) -> str:
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    mesh = c2_mesh(args.n)
+    mesh = hex_cube_mesh(args.n)
     vals, secs = [], []
     for _ in range(args.warmup):
         cpu_baseline(args, mesh, layers=1)
@@ -696,10 +696,10 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": c2_workload_name(args.n),
+            "config": {"workload": workload_name(args.n),
                        "sample": f"{args.ref_layers} cell layers ({E} elements) per step"},
             "cpu_baseline": {"value": v, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.ref_layers} of 128 cell layers per step"},
+                             "sample": f"{args.ref_layers} of {args.n} cell layers per step"},
             "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -719,8 +719,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the raw nvidia-smi clock samples of the timed region are written")
-    ap.add_argument("--configs", default="c3,c4,c5",
-                    help="other workloads timed after the headline one (comma list of c3, c4, c5; '' for none)")
+    ap.add_argument("--workloads", "--configs", dest="workloads", default="hybrid,j2,batch",
+                    help="other workloads timed after the headline one (comma list of hybrid, j2, batch; "
+                         "'' for none)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

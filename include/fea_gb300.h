@@ -233,15 +233,17 @@ typedef struct {
 
 typedef struct fea_mesh fea_mesh;
 
-/* Message of the last failing call on this thread ("" if none). */
+/* Message of the last failing call on this thread ("" if none).  A service
+ * of the library; no passage of the paper defines it. */
 const char* fea_last_error(void);
 
-/* FEA_ABI_VERSION of the loaded library. */
+/* FEA_ABI_VERSION of the loaded library (service). */
 int fea_abi_version(void);
 
-/* Copy a mesh to the device and prepare it (a1 of the element loop: element
- * lists per type in input order, packed per-type connectivity, offsets of the
- * element-to-nonzero map).  Checks on the host that every type is known, that
+/* Copy a mesh to the device and prepare it: the mesh of one subdomain, whose
+ * elements the loop of Alg. "sequential assembly" visits (Sec. 3.1).  The
+ * handle holds the element lists per type in input order, the packed per-type
+ * connectivity and the offsets of the element-to-nonzero map.  Checks on the host that every type is known, that
  * conn_offsets matches the node count of each type and that node ids are in
  * range (host input), or on the device (device input; then synchronous).
  * n_nodes < 2^31, n_elems < 2^31.  *out receives the handle.
@@ -253,11 +255,12 @@ int fea_mesh_upload(const fea_mesh_desc* desc, void* stream, fea_mesh** out);
  * pointer.  Stream-ordered (a pageable host source is copied before return). */
 int fea_mesh_set_coords(fea_mesh* mesh, const double* coords, int on_device, void* stream);
 
-/* Free a handle and every device buffer it owns (synchronizes the device). */
+/* Free a handle and every device buffer it owns (synchronizes the device).
+ * Service. */
 int fea_mesh_destroy(fea_mesh* mesh);
 
 /* Sizes: nodes, elements, and map_len = sum over elements of n_e^2 (the
- * length of node_map).  Host call, no device work. */
+ * length of node_map).  Service; host call, no device work. */
 int fea_mesh_info(const fea_mesh* mesh, int64_t* n_nodes, int64_t* n_elems, int64_t* map_len);
 
 /* Build the node graph of the mesh inside the handle (Sec. 3.1: nodes i and j
@@ -269,7 +272,9 @@ int fea_mesh_info(const fea_mesh* mesh, int64_t* n_nodes, int64_t* n_elems, int6
 int fea_pattern_size(fea_mesh* mesh, int ndof, int64_t* nnz, void* stream);
 
 /* Write the scalar CSR pattern and the element-to-nonzero map (needs a
- * preceding fea_pattern_size with the same ndof).
+ * preceding fea_pattern_size with the same ndof).  The map gives the
+ * positions the scatter A += P_e^T A^e P_e of Alg. "sequential assembly"
+ * writes, in the square local matrix of Sec. 3.1.
  *  row_ptr_d  int64 [n_nodes*ndof + 1]  row d*i+c starts at row_ptr_d[d*i+c]
  *  col_idx_d  int32 [nnz]               row d*i+c holds columns d*j+c' for the
  *                                       node neighbours j ascending, c' = 0..d-1
@@ -294,8 +299,10 @@ int fea_build_csr_pattern(fea_mesh* mesh, int ndof, int64_t* row_ptr_d, int32_t*
 int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d,
                  const int32_t* node_map_d, double* A_vals_d, double* b_d, void* stream);
 
-/* Work items of the persistent schedules (fea_schedule): for each element
- * type t in enum order, the elements of type t in upload order cut into runs
+/* Work items of the persistent schedules (fea_schedule), the counterpart of
+ * the chunks of elements the paper's loop scheduling hands to threads (Sec.
+ * 3.2.1; their size is studied in Sec. 5.2): for each element type t in enum
+ * order, the elements of type t in upload order cut into runs
  * of at most chunk elements (chunk 0 = 128).  Item i covers the elements of
  * type type_h[i] with in-type ranks first_h[i] .. first_h[i] + count_h[i] - 1.
  * *n_items receives the count; the three host arrays (each may be NULL) need
@@ -303,7 +310,8 @@ int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_
 int fea_work_items(const fea_mesh* mesh, int chunk, int64_t* n_items, int32_t* type_h, int32_t* first_h,
                    int32_t* count_h);
 
-/* Grid size of the persistent launch of op on mesh: op->n_ctas if positive,
+/* Grid size of the persistent launch of op on mesh (the workers that share
+ * the items, Sec. 4): op->n_ctas if positive,
  * else the number of CTAs resident at once (occupancy x SM count), which is
  * how many queues a FEA_SCHED_QUEUES packing should fill.  Host call. */
 int fea_persistent_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
@@ -320,7 +328,7 @@ int fea_persistent_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
  * return map latches FEA_ERR_NO_CONVERGENCE. */
 int fea_element_loop(const fea_operator* op, fea_mesh* mesh, double* stress_d, void* stream);
 
-/* Grid size of the persistent element loop (as fea_persistent_grid). */
+/* Grid size of the persistent element loop (as fea_persistent_grid, Sec. 4). */
 int fea_element_loop_grid(const fea_operator* op, fea_mesh* mesh, int* n_ctas);
 
 /* Product of an assembled system with a vector, and the partial-row form of
@@ -398,7 +406,8 @@ int fea_pack_lpt(const double* cost_h, int64_t n_items, int n_queues, int32_t* q
                  double* load_h);
 
 /* ---------------------------------------------------------------------------
- * Batches: many independent meshes of uneven sizes assembled by one
+ * Batches: many independent meshes of uneven sizes (the uneven per-unit work
+ * that the load balancing of Sec. 4 evens out) assembled by one
  * persistent launch (a zeroing kernel, then CTAs that take work items of any
  * (mesh, element type) by work stealing), optionally captured once as a CUDA
  * graph and replayed.  Each entry names a mesh whose pattern and map were
@@ -471,16 +480,18 @@ int fea_batch_latency(fea_batch* batch, uint64_t* mesh_ns_h, void* stream);
  * call). */
 int fea_row_ptr_from_counts_noalloc(const int32_t* counts_d, int64_t n, int64_t* row_ptr_d, void* stream);
 
-/* Nodes per CTA block of FEA_SCATTER_ROWS (default 64; 1..512).  A change
+/* Nodes per CTA block of FEA_SCATTER_ROWS (the full-row decomposition of Sec.
+ * 3.1 applied per CTA; default 64; 1..512).  A change
  * drops the current plan; the next ROWS assembly rebuilds it.  Host call. */
 int fea_mesh_set_rows_block(fea_mesh* mesh, int block_nodes);
 
-/* Elements per block of FEA_SCATTER_BLOCK (default 64; 1..108, the blocks'
+/* Elements per block of FEA_SCATTER_BLOCK (the local partitioning of Sec.
+ * 3.2.1; default 64; 1..108, the blocks'
  * geometry is staged in shared memory).  A change drops the current plan.
  * Host call. */
 int fea_mesh_set_block_elems(fea_mesh* mesh, int block_elems);
 
-/* Statistics of the current FEA_SCATTER_ROWS plan (zeros if none):
+/* Statistics of the current FEA_SCATTER_ROWS plan (Sec. 3.1; zeros if none):
  * info[0] blocks, [1] nodes per block, [2] max local nodes of a block,
  * [3] max halo elements of a block, [4] entry tasks, [5] element
  * contributions, [6] halo elements (with repeats), [7] plan bytes on the
@@ -488,7 +499,9 @@ int fea_mesh_set_block_elems(fea_mesh* mesh, int block_elems);
 int fea_rows_plan_info(const fea_mesh* mesh, int64_t info[8]);
 
 /* The FEA_SCATTER_MULTIDEP plan for subdomains of `chunk` elements (0 = 128),
- * built if the mesh holds none for that chunk (host work, synchronous).
+ * built if the mesh holds none for that chunk (host work, synchronous): the
+ * subdomains and their neighbour lists that the commutative multidependences
+ * of Sec. 3.2.2 (Alg. "multideps") exclude each other by.
  *  info        int64 [4]: subdomains, neighbour-list entries, largest list,
  *              most local colors of a subdomain
  *  nb_off_h    NULL or int64 [subdomains + 1] (host): offsets into nb_h
@@ -504,25 +517,25 @@ int fea_multidep_plan(fea_mesh* mesh, int chunk, int64_t info[4], int64_t* nb_of
                       int32_t* color_h);
 
 /* Hold (held = 1) or free (0) the lock of one subdomain of the mesh's
- * FEA_SCATTER_MULTIDEP plan in every later launch, as if a CTA that never
+ * FEA_SCATTER_MULTIDEP plan (Sec. 3.2.2) in every later launch, as if a CTA that never
  * finishes owned it: the subdomains whose lists contain it can then never
  * run, and the CTAs give up after lock_timeout_us with FEA_ERR_TIMEOUT.  For
  * tests of the bounded wait.  Host call; FEA_ERR_ARG without a plan or for a
  * subdomain out of range. */
 int fea_multidep_hold(fea_mesh* mesh, int subdomain, int held);
 
-/* The element coloring of FEA_SCATTER_COLOR (built by the first COLOR
- * assembly): *n_colors classes, and, if colors_h is not NULL, the class of
+/* The element coloring of FEA_SCATTER_COLOR (Sec. 3.2.1, Alg. "coloring";
+ * built by the first COLOR assembly): *n_colors classes, and, if colors_h is not NULL, the class of
  * every element (int32 [n_elems], host).  No two elements of one class share
  * a node.  Host call; FEA_ERR_ARG if no coloring exists yet. */
 int fea_color_info(const fea_mesh* mesh, int32_t* colors_h, int* n_colors);
 
 /* Number of kernels one fea_assemble call with this operator launches on this
- * mesh (after its pattern is built).  Host call. */
+ * mesh (after its pattern is built).  Service; host call. */
 int fea_assemble_launches(const fea_operator* op, const fea_mesh* mesh, int* n_kernels);
 
 /* Wait for the stream and return the mesh's latched device status (and clear
- * it).  FEA_ERR_INVERTED_ELEMENT names the first element id found in the
+ * it).  Service.  FEA_ERR_INVERTED_ELEMENT names the first element id found in the
  * message.  Synchronous. */
 int fea_check(fea_mesh* mesh, void* stream);
 

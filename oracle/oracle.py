@@ -247,7 +247,7 @@ J2_DEFAULTS = dict(young=1.0, poisson=0.3, sigma0=1e-3, sigma_inf=3e-3, delta=30
 
 
 def j2_params(**kw) -> np.ndarray:
-    """Material and Newton parameters in the oracle's order (defaults: the C4 workload)."""
+    """Material and Newton parameters in the oracle's order (defaults: those of the 96^3 elastoplastic hex workload)."""
     p = dict(J2_DEFAULTS, **kw)
     return np.array([p["young"], p["poisson"], p["sigma0"], p["sigma_inf"], p["delta"], p["hardening"],
                      p["tol_g"], p["tol_step"], p["max_iter"]], dtype=np.float64)

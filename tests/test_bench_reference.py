@@ -25,7 +25,7 @@ def test_reference_arm_prints_one_line_with_the_workload_name():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "elements/s" and d["higher_is_better"] is True
     assert d["metric"] == bench.METRIC
-    assert d["config"]["workload"] == bench.c2_workload_name(8)
+    assert d["config"]["workload"] == bench.workload_name(8)
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
 
@@ -37,7 +37,7 @@ def test_workload_name_counts_the_lattice_nonzeros():
     from paper_1805_03949_gb300 import meshgen as mg
     for n in (1, 2, 5):
         rp, cols, _ = oracle.pattern(mg.hex_cube(n, 0.2, 2), 3)
-        assert f"{len(cols):,} nonzeros" in bench.c2_workload_name(n)
+        assert f"{len(cols):,} nonzeros" in bench.workload_name(n)
 
 
 def test_other_ranks_print_nothing():

@@ -48,7 +48,7 @@ def _check_rows(oracle, s, mesh, nodes, op_oracle, d, tol, **params):
 
 
 @pytest.fixture(scope="module")
-def c2():
+def hex128():
     fea = engine()
     n = 128
     mesh = mg.hex_cube(n, 0.2, 2)
@@ -57,8 +57,8 @@ def c2():
     s.close()
 
 
-def test_c2_pattern_closed_form(c2):
-    fea, mesh, s = c2
+def test_hex128_pattern_closed_form(hex128):
+    fea, mesh, s = hex128
     n = 128
     assert s.A.numel() == 9 * (3 * n + 1) ** 3 == 513_599_625
     rp = s.row_ptr.cpu().numpy()
@@ -84,8 +84,8 @@ def test_c2_pattern_closed_form(c2):
 
 @pytest.mark.parametrize("scatter", [3, 0, 1, 2, 4])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_c2_sampled_rows(oracle, c2, precision, scatter):
-    fea, mesh, s = c2
+def test_hex128_sampled_rows(oracle, hex128, precision, scatter):
+    fea, mesh, s = hex128
     op = fea.make_operator(kind=1, precision=precision, scatter=scatter, young=1.0, poisson=0.3)
     s.A.fill_(float("nan"))
     s.assemble(op)
@@ -98,7 +98,7 @@ def test_c2_sampled_rows(oracle, c2, precision, scatter):
     assert np.allclose(bsum, 1.0, rtol=0, atol=1e-9 if precision == 0 else 1e-5)
 
 
-def test_c3_hybrid_sampled_rows(oracle):
+def test_hybrid100_sampled_rows(oracle):
     fea = engine()
     mesh = mg.hybrid_cube(100, 3)
     s = fea.System.from_mesh(mesh, 1, with_cols=True)
@@ -118,11 +118,11 @@ def test_c3_hybrid_sampled_rows(oracle):
         s.close()
 
 
-def test_c2_product_sampled_rows(c2):
+def test_hex128_product_sampled_rows(hex128):
     """y = A x on the full system, in the bench's call: sampled rows recomputed
     on the CPU from the same A and the column indices."""
     import torch
-    fea, mesh, s = c2
+    fea, mesh, s = hex128
     s.assemble(fea.make_operator(kind=1, precision=0, young=1.0, poisson=0.3))
     x = torch.randn(s.b.numel(), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
     y = torch.full_like(x, float("nan"))
@@ -161,9 +161,9 @@ def _nh_rows(oracle, mesh, U, nodes, **kw):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-def test_c2_finite_strain_sampled_rows(oracle, c2, precision):
+def test_hex128_finite_strain_sampled_rows(oracle, hex128, precision):
     import torch
-    fea, mesh, s = c2
+    fea, mesh, s = hex128
     U = mg.fourier_displacement(mesh.coords, 0.004, seed=6) + 0.05 * mesh.coords[:, [1, 2, 0]]
     u = torch.tensor(U.reshape(-1), device="cuda")
     s.A.fill_(float("nan"))
