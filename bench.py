@@ -118,6 +118,30 @@ class ClockSampler:
 # workload and algorithmic counts
 # ---------------------------------------------------------------------------
 
+# The assembly variants of the headline workload: name -> (fea_precision,
+# fea_scatter suffix).  "fp32a" is FP32 geometry with the FP64 redo of
+# distorted elements only (kappa_F(J) > 12); the multidependence variant runs
+# subdomains of 128 elements under neighbour-set locks.
+VARIANTS = {
+    "fp64_atomic": (0, "ATOMIC"),
+    "fp32_atomic": (1, "ATOMIC"),
+    "fp32_rows": (1, "ROWS"),
+    "fp64_rows": (0, "ROWS"),
+    "fp32_color": (1, "COLOR"),
+    "fp32_block": (1, "BLOCK"),
+    "fp32_multidep": (1, "MULTIDEP"),
+    "fp32a_atomic": (2, "ATOMIC"),
+    "fp32a_rows": (2, "ROWS"),
+}
+
+
+def variant_operators(fea) -> dict:
+    """Linear elasticity (E = 1, nu = 0.3) operators of the variants, in table order."""
+    return {name: fea.make_operator(kind=fea.FEA_OP_ELASTICITY, precision=prec,
+                                    scatter=getattr(fea, "FEA_SCATTER_" + sc), poisson=0.3)
+            for name, (prec, sc) in VARIANTS.items()}
+
+
 def hex_cube_mesh(n=128):
     from paper_1805_03949_gb300 import meshgen as mg
     return mg.hex_cube(n, 0.2, 2)
@@ -202,19 +226,7 @@ def run_ours(args, rank, world, local_rank):
     nnz = sysm.A.numel()
     E, N = sysm.n_elems, sysm.n_nodes
 
-    variants = {
-        "fp64_atomic": fea.make_operator(kind=1, precision=0, scatter=fea.FEA_SCATTER_ATOMIC, poisson=0.3),
-        "fp32_atomic": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_ATOMIC, poisson=0.3),
-        "fp32_rows": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_ROWS, poisson=0.3),
-        "fp64_rows": fea.make_operator(kind=1, precision=0, scatter=fea.FEA_SCATTER_ROWS, poisson=0.3),
-        "fp32_color": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_COLOR, poisson=0.3),
-        "fp32_block": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_BLOCK, poisson=0.3),
-        # commutative multidependences: subdomains of 128 elements under neighbour-set locks
-        "fp32_multidep": fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_MULTIDEP, poisson=0.3),
-        # FP32 geometry with the FP64 redo of distorted elements only (kappa_F(J) > 12)
-        "fp32a_atomic": fea.make_operator(kind=1, precision=2, scatter=fea.FEA_SCATTER_ATOMIC, poisson=0.3),
-        "fp32a_rows": fea.make_operator(kind=1, precision=2, scatter=fea.FEA_SCATTER_ROWS, poisson=0.3),
-    }
+    variants = variant_operators(fea)
     if args.block_nodes:
         fea.fea_mesh_set_rows_block(sysm.handle, args.block_nodes)
     if args.only:
@@ -704,7 +716,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -722,7 +734,15 @@ def main():
     ap.add_argument("--workloads", "--configs", dest="workloads", default="hybrid,j2,batch",
                     help="other workloads timed after the headline one (comma list of hybrid, j2, batch; "
                          "'' for none)")
+    return ap
+
+
+def main():
+    ap = make_parser()
     args = ap.parse_args()
+    unknown = sorted({v for v in args.only.split(",") if v} - set(VARIANTS))
+    if unknown:
+        ap.error(f"unknown --only variant(s) {', '.join(unknown)}; known: {', '.join(VARIANTS)}")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
