@@ -65,47 +65,6 @@ __device__ __forceinline__ double f32_to_f64_exact(float x) {
   return __hiloint2double((int)hi, (int)(m << 29));
 }
 
-// Error-free accumulation of FP32 terms in a (hi, lo) pair (Knuth's TwoSum):
-// hi + lo carries about 48 significant bits, so the sum of the FP32 element
-// contributions is formed with FP64-grade accuracy using FP32 instructions.
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  lo += (hi - (s - bb)) + (v - bb);
-  hi = s;
-}
-
-// The FP64 value of hi + lo (one final rounding), with integer instructions.
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-  if (lo == 0.0f) return f32_to_f64_exact(hi);  // a single term: exact widening
-  {  // renormalise so that |lo| <= ulp(hi) / 2
-    const float s = hi + lo;
-    const float bb = s - hi;
-    lo = (hi - (s - bb)) + (lo - bb);
-    hi = s;
-  }
-  if (lo == 0.0f) return f32_to_f64_exact(hi);
-  const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
-  const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
-  if (eh == 0 || eh == 255 || el == 0) return f32_to_f64_exact(hi) + f32_to_f64_exact(lo);  // rare
-  // significands in units of the FP64 ulp of hi: hi = MH, lo = ML * 2^shift (shift <= 5)
-  const uint64_t MH = (uint64_t)((uh & 0x7fffffu) | 0x800000u) << 29;
-  const uint64_t ML = (uint64_t)((ul & 0x7fffffu) | 0x800000u);
-  const int shift = el - eh + 29;
-  const uint64_t L = shift >= 0 ? (ML << shift) : (shift > -60 ? (ML >> (-shift)) : 0ull);
-  uint64_t M = ((uh ^ ul) & 0x80000000u) ? MH - L : MH + L;
-  int ex = eh;
-  if (M >= (1ull << 53)) {
-    M >>= 1;
-    ++ex;
-  } else if (M < (1ull << 52)) {
-    M <<= 1;
-    --ex;
-  }
-  const uint64_t bits = ((uint64_t)(uh & 0x80000000u) << 32) | ((uint64_t)(ex + 896) << 52) | (M & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
-}
-
 // cofactor matrix C of J (J^{-1} = C^T / det J, det J = J_0j C_0j)
 __device__ __forceinline__ void cofactors(const double J[3][3], double C[3][3]) {
   C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
