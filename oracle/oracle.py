@@ -221,19 +221,6 @@ def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_co
     return out
 
 
-def err_metric(a, ref, S):
-    """max |a - ref| / S over entries with S > 0, and whether S == 0 entries match exactly.
-
-    S is the oracle's magnitude sum: the same formula with every factor taken
-    in absolute value, the scale of the a-priori rounding error bound.
-    """
-    a = np.asarray(a, dtype=np.float64); ref = np.asarray(ref, dtype=np.float64); S = np.asarray(S)
-    pos = S > 0
-    err = float(np.max(np.abs(a[pos] - ref[pos]) / S[pos])) if pos.any() else 0.0
-    zeros_ok = bool(np.all(a[~pos] == 0.0) and np.all(ref[~pos] == 0.0))
-    return err, zeros_ok
-
-
 # ---------------------------------------------------------------------------
 # J2 plasticity with Voce hardening (j2_oracle.c)
 # ---------------------------------------------------------------------------

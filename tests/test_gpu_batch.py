@@ -1,6 +1,5 @@
 """GPU parity of batched assembly: many meshes in one persistent launch, direct
 and replayed as a CUDA graph, after autotuning; per-mesh latencies."""
-import numpy as np
 import pytest
 
 from paper_1805_03949_gb300 import meshgen as mg
