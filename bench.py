@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-NOMINAL_FP64_TFLOPS = 1.25     # GB300 FP64 (nominal, profiling recipe)
+NOMINAL_FP64_TFLOPS = 1.25     # GB300 FP64, NVIDIA's nominal dense rate
 NOMINAL_FP32_TFLOPS = 80.5     # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, same GB300"
@@ -46,7 +46,7 @@ METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, sam
 # ncu capture of the 64^3 case (same kernel and launch shape, inputs larger than
 # L2) scaled by the element count, which its traffic grows with.  Remove an
 # entry whenever its kernel changes.
-TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.969472e6 + 468.289792e6),
+TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.967936e6 + 465.030656e6),
                  "k_block_pipe": 8.0 * (415.417088e6 + 575.375360e6)}
 
 # the kernel each variant spends its step in
