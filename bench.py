@@ -389,7 +389,7 @@ def run_ours(args, rank, world, local_rank):
         if kind in ("rows", "block") and not fused and r["geo_ms"] > r["main_ms"]:
             k_name, k_ms = "k_geometry", r["geo_ms"]
             roof = {"bound": "alu", "achieved": fl["fp64_geometry"] / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
-                    "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (recipe table)",
+                    "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (NVIDIA, dense)",
                     "work": "FP64 geometry"}
         elif kind in ("rows", "block") and not fused:
             k_name, k_ms = DOMINANT_KERNEL[kind], r["main_ms"]
@@ -405,7 +405,7 @@ def run_ours(args, rank, world, local_rank):
             f64 = fl["fp64"] if on_sm else fl["fp64_geometry"]
             if "fp32_" in head and f64 / p64 > by / (hbm * 1e9):
                 roof = {"bound": "alu", "achieved": f64 / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
-                        "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (recipe table)",
+                        "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (NVIDIA, dense)",
                         "work": "FP64 geometry + the minimal FP64 accumulation adds" if on_sm else "FP64 geometry"}
             else:
                 roof = {"bound": "hbm", "achieved": by / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
