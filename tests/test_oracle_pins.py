@@ -205,6 +205,61 @@ def test_prism6_right_prism_matches_exact_integration(oracle):
     assert np.allclose(Ae, exact, rtol=0, atol=1e-14 * np.abs(exact).max())
 
 
+def _sym_ref_pyramid_tensors():
+    """Exact T[a, b, p, q] = int dN_a/dxi_p dN_b/dxi_q and NI[a] = int N_a over
+    the reference pyramid (base [-1,1]^2 at zeta = 0, apex (0,0,1)), for the
+    rational basis N_a = 1/4 [(1 + s_a x)(1 + t_a y) - z + s_a t_a x y z / (1 - z)],
+    N_5 = z (Bedrosian 1992).  The collapsed map x = u (1 - z), y = v (1 - z)
+    (volume factor (1 - z)^2) makes every integrand a polynomial in (u, v, z)."""
+    sp = pytest.importorskip("sympy")
+    x, y, z, u, v = sp.symbols("x y z u v")
+    base = [(-1, -1), (1, -1), (1, 1), (-1, 1)]
+    N = [sp.Rational(1, 4) * ((1 + s * x) * (1 + t * y) - z + s * t * x * y * z / (1 - z)) for s, t in base] + [z]
+    G = [[sp.diff(n, w) for w in (x, y, z)] for n in N]
+    sub = {x: u * (1 - z), y: v * (1 - z)}
+    box = [(u, -1, 1), (v, -1, 1), (z, 0, 1)]
+
+    def integral(f):
+        return sp.integrate(sp.expand(sp.cancel(f.subs(sub) * (1 - z) ** 2)), *box)
+
+    T = np.zeros((5, 5, 3, 3))
+    for a in range(5):
+        for b in range(a, 5):
+            for p in range(3):
+                for q in range(3):
+                    T[a, b, p, q] = T[b, a, q, p] = float(integral(G[a][p] * G[b][q]))
+    NI = np.array([float(integral(n)) for n in N])
+    return T, NI
+
+
+def test_pyr5_affine_pyramid_matches_exact_integration(oracle):
+    """The 8-point collapsed rule integrates the stiffness of an affine pyramid
+    exactly, so the oracle's element must equal the exact integral."""
+    T, NI = _sym_ref_pyramid_tensors()
+    assert NI.sum() == pytest.approx(4.0 / 3.0, rel=1e-15)
+    rng = np.random.default_rng(17)
+    A = np.eye(3) + rng.uniform(-0.3, 0.3, (3, 3))
+    assert np.linalg.det(A) > 0
+    X = np.array(REF_NODES[mg.PYR5], dtype=float) @ A.T + np.array([0.4, -1.2, 2.0])
+    Ai = np.linalg.inv(A)
+    P = np.linalg.det(A) * np.einsum("pk,ql,abpq->abkl", Ai, Ai, T)     # physical-gradient products
+    Ae, be, _, _ = oracle.element(mg.PYR5, X, oracle.OP_DIFFUSION, k0=1.0, k2=0.0, source=1.5)
+    exact = np.einsum("abkk->ab", P)
+    assert np.allclose(Ae, exact, rtol=0, atol=1e-14 * np.abs(exact).max())
+    assert np.allclose(be, 1.5 * np.linalg.det(A) * NI, rtol=1e-14, atol=0)
+    E, nu = 2.1, 0.33
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu)); mu = E / (2 * (1 + nu))
+    Ke, _, _, _ = oracle.element(mg.PYR5, X, oracle.OP_ELASTICITY, young=E, poisson=nu)
+    K = np.zeros((15, 15))
+    for a in range(5):
+        for b in range(5):
+            for c in range(3):
+                for cc in range(3):
+                    K[3 * a + c, 3 * b + cc] = (lam * P[a, b, c, cc] + mu * P[a, b, cc, c]
+                                                + (mu * np.trace(P[a, b]) if c == cc else 0.0))
+    assert np.allclose(Ke, K, rtol=0, atol=1e-13 * np.abs(K).max())
+
+
 @pytest.mark.parametrize("rule", [0, 1])
 def test_tet4_affine_closed_form(oracle, rule):
     rng = np.random.default_rng(5)
