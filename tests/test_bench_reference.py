@@ -28,6 +28,14 @@ def test_reference_arm_prints_one_line_with_the_workload_name():
     assert d["config"]["workload"] == bench.workload_name(8)
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert (d["n_gpus"], d["steps"], d["warmup"], d["scaling"], d["vs_baseline"]) == (1, 1, 0, "weak", None)
+    assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
+    assert d["cpu_baseline"]["cores"] == 1 and d["cpu_baseline"]["unit"] == d["unit"]
+    assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert d["e2e"]["unit"] == d["unit"] and d["e2e"]["d2h_bytes_per_step"] == 0
 
 
 def test_workload_name_counts_the_lattice_nonzeros():
