@@ -142,7 +142,7 @@ def test_element_jacobian_is_the_force_derivative(oracle, etype):
     np.testing.assert_allclose(r["A"], r["A"].T, rtol=0, atol=1e-13 * scale)   # hyperelastic: symmetric
 
 
-@pytest.mark.parametrize("etype", [mg.TET4, mg.HEX8])
+@pytest.mark.parametrize("etype", [mg.TET4, mg.PYR5, mg.PRISM6, mg.HEX8])
 def test_element_force_is_the_energy_derivative(oracle, etype):
     X = ELEMS[etype]
     U = _U(X, seed=9)
@@ -158,7 +158,7 @@ def test_element_force_is_the_energy_derivative(oracle, etype):
     np.testing.assert_allclose(r["b"], g, rtol=0, atol=1e-8 * np.abs(g).max())
 
 
-@pytest.mark.parametrize("etype", [mg.TET4, mg.PRISM6, mg.HEX8])
+@pytest.mark.parametrize("etype", [mg.TET4, mg.PYR5, mg.PRISM6, mg.HEX8])
 def test_finite_rigid_rotation_is_stress_free_and_rotates_the_jacobian(oracle, etype):
     X = ELEMS[etype]
     U = _U(X, seed=11)
