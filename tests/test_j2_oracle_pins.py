@@ -163,13 +163,20 @@ def _rigid_modes(X):
     return modes
 
 
-@pytest.mark.parametrize("etype", [mg.HEX8, mg.TET4, mg.PRISM6])
-def test_element_invariants(oracle, etype):
+NODES = {mg.TET4: 4, mg.PYR5: 5, mg.PRISM6: 6, mg.HEX8: 8}
+ALL_TYPES = [mg.HEX8, mg.TET4, mg.PYR5, mg.PRISM6]
+
+
+def _element(etype):
     if etype == mg.HEX8:
-        X = _hex_element()
-    else:
-        m = mg.template_cube(1, etype, 0.0)
-        X = m.coords[m.conn[: {mg.TET4: 4, mg.PRISM6: 6}[etype]]]
+        return _hex_element()
+    m = mg.template_cube(1, etype, 0.0)
+    return m.coords[m.conn[:NODES[etype]]].copy()
+
+
+@pytest.mark.parametrize("etype", ALL_TYPES)
+def test_element_invariants(oracle, etype):
+    X = _element(etype)
     nn = X.shape[0]
     U = 4e-3 * np.sin(3.0 * X + np.array([0.3, 1.1, 2.0]))
     r = oracle.j2_element(etype, X, U)
@@ -183,15 +190,38 @@ def test_element_invariants(oracle, etype):
         assert np.abs(A @ mode).max() <= 1e-13 * scale * np.abs(mode).max()
 
 
-def test_elastic_element_equals_linear_elasticity(oracle):
+@pytest.mark.parametrize("etype", ALL_TYPES)
+def test_elastic_element_equals_linear_elasticity(oracle, etype):
     """Below yield: tangent = the linear elastic element matrix, f_int = K u."""
-    X = _hex_element()
+    X = _element(etype)
     U = 1e-6 * np.cos(2.0 * X)
-    r = oracle.j2_element(mg.HEX8, X, U)
+    r = oracle.j2_element(etype, X, U)
     assert r["yielded"].sum() == 0
-    K, _, _, _ = oracle.element(mg.HEX8, X, oracle.OP_ELASTICITY, young=E, poisson=NU, body_force=(0, 0, 0))
+    K, _, _, _ = oracle.element(etype, X, oracle.OP_ELASTICITY, young=E, poisson=NU, body_force=(0, 0, 0),
+                                tet_rule=1)
     np.testing.assert_allclose(r["A"], K, rtol=0, atol=1e-14 * np.abs(K).max())
     np.testing.assert_allclose(r["b"], K @ U.reshape(-1), rtol=0, atol=1e-13 * np.abs(K).max() * 1e-6)
+
+
+@pytest.mark.parametrize("etype", ALL_TYPES)
+def test_element_tangent_is_the_force_derivative(oracle, etype):
+    """In the plastic range the element matrix is the derivative of the
+    internal force with respect to the nodal displacements (the committed
+    state fixed): central differences, no point changing between elastic and
+    plastic under the perturbation."""
+    X = _element(etype) + np.random.default_rng(3).uniform(-0.05, 0.05, (NODES[etype], 3))
+    U = 4e-3 * np.sin(3.0 * X + np.array([0.3, 1.1, 2.0]))
+    r = oracle.j2_element(etype, X, U)
+    assert r["yielded"].sum() > 0
+    n, h = U.size, 1e-9
+    Kfd = np.zeros((n, n))
+    for j in range(n):
+        d = np.zeros(n); d[j] = h
+        rp = oracle.j2_element(etype, X, (U.reshape(-1) + d).reshape(U.shape))
+        rm = oracle.j2_element(etype, X, (U.reshape(-1) - d).reshape(U.shape))
+        assert (rp["yielded"] == r["yielded"]).all() and (rm["yielded"] == r["yielded"]).all()
+        Kfd[:, j] = (rp["b"] - rm["b"]) / (2 * h)
+    np.testing.assert_allclose(r["A"], Kfd, rtol=0, atol=1e-7 * np.abs(r["A"]).max())
 
 
 def test_global_assembly_invariants(oracle):
