@@ -260,6 +260,26 @@ def test_pyr5_affine_pyramid_matches_exact_integration(oracle):
     assert np.allclose(Ke, K, rtol=0, atol=1e-13 * np.abs(K).max())
 
 
+def test_tet4_variable_coefficient_closed_form(oracle):
+    """k(x) = k0 + k2 x^2 at the physical x of the points: on a tet the
+    gradients are constant, so A = (int k dV) G G^T.  The 4-point rule is
+    exact for the quadratic k: int x^2 dV = V/20 (sum_a x_a^2 + (sum_a x_a)^2),
+    from int lambda_a lambda_b dV = V (1 + delta_ab) / 20.  The 1-point rule
+    takes k at the centroid."""
+    rng = np.random.default_rng(23)
+    X = np.array([[0.3, -0.2, 0.1], [1.4, 0.1, 0.0], [0.5, 1.2, 0.2], [0.6, 0.4, 1.3]]) + rng.uniform(-0.1, 0.1, (4, 3))
+    E = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], axis=1)
+    V = np.linalg.det(E) / 6.0
+    G = np.array([[-1, -1, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float) @ np.linalg.inv(E)
+    k0, k2 = 0.7, 2.3
+    x = X[:, 0]
+    int_k = k0 * V + k2 * V / 20.0 * (np.sum(x ** 2) + np.sum(x) ** 2)
+    A4, _, _, _ = oracle.element(mg.TET4, X, oracle.OP_DIFFUSION, tet_rule=1, k0=k0, k2=k2)
+    np.testing.assert_allclose(A4, int_k * G @ G.T, rtol=1e-13, atol=1e-15)
+    A1, _, _, _ = oracle.element(mg.TET4, X, oracle.OP_DIFFUSION, tet_rule=0, k0=k0, k2=k2)
+    np.testing.assert_allclose(A1, (k0 + k2 * x.mean() ** 2) * V * G @ G.T, rtol=1e-13, atol=1e-15)
+
+
 @pytest.mark.parametrize("rule", [0, 1])
 def test_tet4_affine_closed_form(oracle, rule):
     rng = np.random.default_rng(5)
