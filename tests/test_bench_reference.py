@@ -1,10 +1,13 @@
 """The reference arm of bench.py (the oracle timed on the host cores) runs on
 CPU and prints one JSON line carrying the same metric and workload name as
-the GPU arm, for one process and for two ranks (only rank 0 prints)."""
+the GPU arm, for one process and for two ranks (only rank 0 prints); and the
+bench's algorithmic counts against brute-force counts on small meshes."""
 import json
 import os
 import subprocess
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -57,7 +60,6 @@ def test_fp64_accumulation_count_matches_brute_force():
     blocks (i <= j) and of b, (contributions - 1), counted element by element
     on small meshes against the closed form in the bench."""
     import bench
-    import numpy as np
     from paper_1805_03949_gb300 import meshgen as mg
     for n, jit in ((1, 0.0), (3, 0.2), (4, 0.1)):
         mesh = mg.hex_cube(n, jit, 2)
@@ -78,3 +80,19 @@ def test_fp64_accumulation_count_matches_brute_force():
         nnz = 9 * (3 * n + 1) ** 3
         fl = bench.algorithmic_flops_hex_elasticity(mesh.n_elems, mesh.n_nodes, nnz)
         assert fl["fp64_accumulate"] == adds_A + adds_b, n
+
+
+def test_algorithmic_bytes_are_the_arrays_one_assembly_moves():
+    """A written once, b written once, and the inputs read once: coordinates,
+    scalar row starts, connectivity and the element-to-nonzero map, each
+    counted from the arrays of a small hex mesh and the oracle's pattern."""
+    import bench
+    from oracle import oracle
+    from paper_1805_03949_gb300 import meshgen as mg
+    for n in (1, 3):
+        mesh = mg.hex_cube(n, 0.2, 2)
+        rp, cols, nmap = oracle.pattern(mesh, 3)
+        b = np.zeros(3 * mesh.n_nodes)
+        moved = (8 * len(cols) + b.nbytes + mesh.coords.astype(np.float64).nbytes + 8 * (len(rp) - 1)
+                 + mesh.conn.astype(np.int32).nbytes + nmap.astype(np.int32).nbytes)
+        assert bench.algorithmic_bytes(mesh.n_nodes, mesh.n_elems, len(cols)) == moved, n
