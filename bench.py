@@ -156,6 +156,15 @@ def algorithmic_bytes(n_nodes, n_elems, nnz, nn=8, ndof=3):
     return 8 * nnz + n_nodes * (24 + 8 * ndof + 8 * ndof) + n_elems * (4 * nn + 4 * nn * nn)
 
 
+def algorithmic_bytes_spmv(n_nodes, nnz, ndof=3):
+    """Bytes of y = A x read through the node graph: A once, one int32 node
+    column per node-level nonzero, the node row starts, the scalar row starts,
+    x read once and y written once."""
+    nnz_node = nnz // (ndof * ndof)
+    return (8 * nnz + 4 * nnz_node + 8 * (n_nodes + 1) + 8 * (ndof * n_nodes + 1)
+            + 8 * ndof * n_nodes + 8 * ndof * n_nodes)
+
+
 def algorithmic_flops_hex_elasticity(n_elems, n_nodes, nnz, nq=8, nn=8):
     """FP32 and FP64 arithmetic of one FP32-integrate hex8 elasticity assembly (FMA = 2 flop).
 
@@ -293,8 +302,7 @@ def run_ours(args, rank, world, local_rank):
         x = torch.randn(sysm.b.numel(), dtype=torch.float64, device=dev)
         y = torch.empty_like(x)
         sp_ms = _time_calls(lambda: fea.fea_spmv(sysm.handle, 3, sysm.row_ptr, sysm.A, x, y), 20)
-        nnz_node = nnz // 9
-        sp_bytes = 8 * nnz + 4 * nnz_node + 8 * (N + 1) + 8 * N + 8 * 3 * N + 8 * 3 * N
+        sp_bytes = algorithmic_bytes_spmv(N, nnz)
         hbm_pk, _ = _peaks()
         # one FP64 FMA per stored value: on GB300 the FP64 pipe bounds the product
         # about as tightly as HBM does, so both fractions are reported

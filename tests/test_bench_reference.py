@@ -96,3 +96,18 @@ def test_algorithmic_bytes_are_the_arrays_one_assembly_moves():
         moved = (8 * len(cols) + b.nbytes + mesh.coords.astype(np.float64).nbytes + 8 * (len(rp) - 1)
                  + mesh.conn.astype(np.int32).nbytes + nmap.astype(np.int32).nbytes)
         assert bench.algorithmic_bytes(mesh.n_nodes, mesh.n_elems, len(cols)) == moved, n
+
+
+def test_spmv_algorithmic_bytes_are_the_arrays_the_product_moves():
+    """A, the node-level columns, the node and scalar row starts, x and y."""
+    import bench
+    from oracle import oracle
+    from paper_1805_03949_gb300 import meshgen as mg
+    for n in (1, 3):
+        mesh = mg.hex_cube(n, 0.2, 2)
+        rp_node, cols_node, _ = oracle.pattern(mesh, 1)
+        rp, cols, _ = oracle.pattern(mesh, 3)
+        x = np.zeros(3 * mesh.n_nodes)
+        moved = (8 * len(cols) + cols_node.astype(np.int32).nbytes + rp_node.astype(np.int64).nbytes
+                 + rp.astype(np.int64).nbytes + 2 * x.nbytes)
+        assert bench.algorithmic_bytes_spmv(mesh.n_nodes, len(cols)) == moved, n
