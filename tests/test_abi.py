@@ -60,12 +60,62 @@ def test_host_side_argument_checks(clib):
     assert b"multidep" in clib.fea_last_error()
 
 
+def test_every_entry_point_rejects_a_null_handle(clib):
+    """Each call with a null handle (or null required output) fails with
+    FEA_ERR_ARG before touching the device; so do out-of-range sizes."""
+    I64, F = ctypes.c_int64, ctypes.c_float
+    n = ctypes.c_int64()
+    k = ctypes.c_int()
+    info = (ctypes.c_int64 * 8)()
+    out = ctypes.c_void_p()
+    calls = {
+        "fea_mesh_set_coords": (None, None, 0, None),
+        "fea_mesh_destroy": (None,),
+        "fea_pattern_size": (None, 3, ctypes.byref(n), None),
+        "fea_build_csr_pattern": (None, 3, None, None, None, None),
+        "fea_work_items": (None, 0, ctypes.byref(n), None, None, None),
+        "fea_persistent_grid": (None, None, ctypes.byref(k)),
+        "fea_element_loop": (None, None, None, None),
+        "fea_element_loop_grid": (None, None, ctypes.byref(k)),
+        "fea_costmodel_destroy": (None,),
+        "fea_costmodel_get_params": (None, None, None),
+        "fea_costmodel_fit_scaler": (None, None, None, I64(0), None),
+        "fea_costmodel_grad": (None, None, None, I64(1), None, None, None),
+        "fea_costmodel_train": (None, None, None, I64(1), 1, F(0.01), None, None),
+        "fea_costmodel_predict": (None, None, I64(0), None, None),
+        "fea_item_features": (None, 0, None, None, None, None),
+        "fea_batch_create": (None, 1, None, ctypes.byref(out)),
+        "fea_batch_destroy": (None,),
+        "fea_batch_set_config": (None, 64, 0),
+        "fea_batch_info": (None, None, None, None),
+        "fea_batch_autotune": (None, 1, None, None, None, None),
+        "fea_batch_capture": (None, None),
+        "fea_batch_assemble": (None, None),
+        "fea_batch_latency": (None, None, None),
+        "fea_row_ptr_from_counts_noalloc": (None, I64(-1), None, None),
+        "fea_mesh_set_rows_block": (None, 64),
+        "fea_mesh_set_block_elems": (None, 64),
+        "fea_rows_plan_info": (None, info),
+        "fea_color_info": (None, None, ctypes.byref(k)),
+        "fea_assemble_launches": (None, None, ctypes.byref(k)),
+        "fea_pack_lpt": (None, I64(1), 1, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(clib, name)(*args) == -1, name
+    params = (ctypes.c_float * 2048)()
+    for n_in in (0, 9):                                   # the network takes 1..8 features
+        assert clib.fea_costmodel_create(n_in, params, ctypes.byref(out)) == -1
+    assert not out.value
+
+
 def test_binding_structs_match_the_header(tmp_path):
     """sizeof and field offsets of the ctypes structs equal the C compiler's view of the header."""
     from paper_1805_03949_gb300 import fea
     probe = tmp_path / "layout.c"
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fea_gb300.h"', 'int main(void) {']
-    for cname, cls in (("fea_operator", fea.fea_operator), ("fea_mesh_desc", fea.fea_mesh_desc)):
+    structs = {"fea_operator": fea.fea_operator, "fea_mesh_desc": fea.fea_mesh_desc,
+               "fea_batch_entry": fea.fea_batch_entry}
+    for cname, cls in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
         for field, _ in cls._fields_:
             lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
@@ -80,8 +130,8 @@ def test_binding_structs_match_the_header(tmp_path):
         if not line:
             continue
         cname, field, value = line.split()
-        cls = fea.fea_operator if cname == "fea_operator" else fea.fea_mesh_desc
+        cls = structs[cname]
         expect = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
         assert int(value) == expect, (cname, field, value, expect)
         seen += 1
-    assert seen == len(fea.fea_operator._fields_) + len(fea.fea_mesh_desc._fields_) + 2
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
