@@ -198,7 +198,9 @@ def test_cost_model_gain_on_a_hybrid_mesh(capsys):
     try:
         r2, res = _study(fea, s, dict(kind=0, precision=1, tet_rule=1, k0=1.0, k2=1.0, source=1.0), 64, {},
                          capsys, "hybrid 40^3 diffusion")
-        assert r2["mlp"] > max(r2["gauss_points"], 0.0) + 0.1
+        # the model leaves at most half the variance of the item costs that
+        # the Gauss-point weights leave unexplained
+        assert 1.0 - r2["mlp"] <= 0.5 * (1.0 - max(r2["gauss_points"], 0.0))
         assert res["mlp"] <= 1.05 * res["gauss_points"]
     finally:
         s.close()
