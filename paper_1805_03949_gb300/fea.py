@@ -130,6 +130,7 @@ _lib = _load()
 
 
 def lib():
+    """The loaded engine library (ctypes.CDLL)."""
     return _lib
 
 
@@ -153,10 +154,12 @@ def _dptr(t) -> ctypes.c_void_p:
 
 
 def fea_last_error() -> str:
+    """Message of the last failing call on this thread."""
     return _lib.fea_last_error().decode()
 
 
 def fea_abi_version() -> int:
+    """ABI version of the loaded library."""
     return int(_lib.fea_abi_version())
 
 
@@ -197,31 +200,37 @@ def fea_mesh_set_coords(h, coords, stream=None):
 
 
 def fea_mesh_destroy(h):
+    """Free a mesh handle and its device buffers."""
     _check(_lib.fea_mesh_destroy(h))
 
 
 def fea_mesh_info(h):
+    """(n_nodes, n_elems, map_len), map_len = sum of n_e^2 over the elements."""
     n, e, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.fea_mesh_info(h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(m)))
     return n.value, e.value, m.value
 
 
 def fea_pattern_size(h, ndof: int, stream=None) -> int:
+    """Build the node graph and return the scalar nonzero count for ndof (1 or 3) dofs per node."""
     nnz = ctypes.c_int64()
     _check(_lib.fea_pattern_size(h, ndof, ctypes.byref(nnz), _stream(stream)))
     return nnz.value
 
 
 def fea_build_csr_pattern(h, ndof: int, row_ptr, col_idx, node_map, stream=None):
+    """Write row_ptr (int64), col_idx (int32, or None) and node_map (int32, or None) CUDA tensors."""
     _check(_lib.fea_build_csr_pattern(h, ndof, _dptr(row_ptr), _dptr(col_idx), _dptr(node_map), _stream(stream)))
 
 
 def fea_assemble(op: "fea_operator", h, row_ptr, node_map, A, b, stream=None):
+    """Overwrite A (float64 [nnz]) and b (float64 [n_nodes * ndof]) with the assembled system."""
     _check(_lib.fea_assemble(ctypes.byref(op), h, _dptr(row_ptr), _dptr(node_map), _dptr(A), _dptr(b),
                              _stream(stream)))
 
 
 def fea_check(h, stream=None):
+    """Wait for the stream; raise FeaError if the mesh latched a device error."""
     _check(_lib.fea_check(h, _stream(stream)))
 
 
@@ -236,14 +245,17 @@ def fea_row_ptr_from_counts_noalloc(counts, row_ptr, stream=None):
 
 
 def fea_mesh_set_rows_block(h, block_nodes: int):
+    """Nodes per CTA block of the owner-computes rows scatter (1..512)."""
     _check(_lib.fea_mesh_set_rows_block(h, int(block_nodes)))
 
 
 def fea_mesh_set_block_elems(h, block_elems: int):
+    """Elements per block of the block-task scatter."""
     _check(_lib.fea_mesh_set_block_elems(h, int(block_elems)))
 
 
 def fea_rows_plan_info(h) -> dict:
+    """Statistics of the mesh's current owner-computes rows plan (zeros if none)."""
     arr = (ctypes.c_int64 * 8)()
     _check(_lib.fea_rows_plan_info(h, arr))
     keys = ["blocks", "block_nodes", "max_local", "max_halo", "tasks", "contributions", "halo_elements", "bytes"]
@@ -276,12 +288,12 @@ def fea_multidep_plan(h, chunk: int, n_elems: int) -> dict:
 
 
 def fea_multidep_hold(h, subdomain: int, held: bool):
+    """Hold or free one subdomain's lock in every later multidependence launch (tests of the bounded wait)."""
     _check(_lib.fea_multidep_hold(h, int(subdomain), 1 if held else 0))
 
 
 def fea_work_items(h, chunk: int = 0):
     """Work items of the persistent schedules: (type, first, count) int32 arrays."""
-    import numpy as np
     n = ctypes.c_int64()
     _check(_lib.fea_work_items(h, chunk, ctypes.byref(n), None, None, None))
     t = np.zeros(n.value, dtype=np.int32); f = np.zeros_like(t); c = np.zeros_like(t)
@@ -291,6 +303,7 @@ def fea_work_items(h, chunk: int = 0):
 
 
 def fea_persistent_grid(op: "fea_operator", h) -> int:
+    """CTAs of the persistent launch of op on the mesh (the queue count for packed schedules)."""
     n = ctypes.c_int32()
     _check(_lib.fea_persistent_grid(ctypes.byref(op), h, ctypes.byref(n)))
     return int(n.value)
@@ -305,7 +318,7 @@ def _np_ptr(a):
 
 
 def fea_costmodel_create(n_in: int, params) -> ctypes.c_void_p:
-    import numpy as np
+    """New cost model with n_in features (1..8) and initial float32 parameters."""
     p = np.ascontiguousarray(params, dtype=np.float32)
     h = ctypes.c_void_p()
     _check(_lib.fea_costmodel_create(n_in, _np_ptr(p), ctypes.byref(h)))
@@ -313,11 +326,12 @@ def fea_costmodel_create(n_in: int, params) -> ctypes.c_void_p:
 
 
 def fea_costmodel_destroy(h):
+    """Free a cost model."""
     _check(_lib.fea_costmodel_destroy(h))
 
 
 def fea_costmodel_get_params(h, n_in: int):
-    import numpy as np
+    """(parameters, scaler) as float32 numpy arrays."""
     n = 32 * n_in + 32 + 32 * 32 + 32 + 32 + 1
     p = np.zeros(n, dtype=np.float32); sc = np.zeros(2 * n_in + 2, dtype=np.float32)
     _check(_lib.fea_costmodel_get_params(h, _np_ptr(p), _np_ptr(sc)))
@@ -325,10 +339,12 @@ def fea_costmodel_get_params(h, n_in: int):
 
 
 def fea_costmodel_fit_scaler(h, X, y, stream=None):
+    """Fit the feature and target standardisation to X [n, n_in] and y [n] (float32 CUDA)."""
     _check(_lib.fea_costmodel_fit_scaler(h, _dptr(X), _dptr(y), X.shape[0], _stream(stream)))
 
 
 def fea_costmodel_grad(h, X, y, n_params: int, stream=None):
+    """(gradient [n_params], loss [1]) at the current parameters, as float32 CUDA tensors."""
     g = torch.empty(n_params, dtype=torch.float32, device=X.device)
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
     _check(_lib.fea_costmodel_grad(h, _dptr(X), _dptr(y), X.shape[0], _dptr(g), _dptr(loss), _stream(stream)))
@@ -336,18 +352,21 @@ def fea_costmodel_grad(h, X, y, n_params: int, stream=None):
 
 
 def fea_costmodel_train(h, X, y, epochs: int, lr: float, stream=None):
+    """Full-batch Adam epochs; returns the last epoch's loss (float32 CUDA [1])."""
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
     _check(_lib.fea_costmodel_train(h, _dptr(X), _dptr(y), X.shape[0], epochs, lr, _dptr(loss), _stream(stream)))
     return loss
 
 
 def fea_costmodel_predict(h, X, stream=None):
+    """Predicted costs for X [n, n_in] (float32 CUDA [n], target units)."""
     y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
     _check(_lib.fea_costmodel_predict(h, _dptr(X), X.shape[0], _dptr(y), _stream(stream)))
     return y
 
 
 def fea_item_features(h, chunk: int, n_items: int, u=None, state_in=None, device="cuda", stream=None):
+    """Features of the work items of fea_work_items(h, chunk): float32 CUDA [n_items, 6]."""
     X = torch.empty((n_items, 6), dtype=torch.float32, device=device)
     _check(_lib.fea_item_features(h, chunk, _dptr(u),
                                   _dptr(state_in), _dptr(X), _stream(stream)))
@@ -356,7 +375,6 @@ def fea_item_features(h, chunk: int, n_items: int, u=None, state_in=None, device
 
 def fea_pack_lpt(costs, n_queues: int):
     """Host LPT packing: (queue ids int32, offsets int64 [n_queues + 1], loads float64)."""
-    import numpy as np
     c = np.ascontiguousarray(costs, dtype=np.float64)
     q = np.zeros(len(c), dtype=np.int32); off = np.zeros(n_queues + 1, dtype=np.int64)
     load = np.zeros(n_queues, dtype=np.float64)
@@ -384,32 +402,38 @@ class Batch:
         _check(_lib.fea_batch_create(ctypes.byref(op), len(self.systems), arr, ctypes.byref(self.handle)))
 
     def set_config(self, chunk: int, n_ctas: int):
+        """Change the work-item size and the grid (drops a captured graph)."""
         _check(_lib.fea_batch_set_config(self.handle, chunk, n_ctas))
 
     def info(self):
+        """Items, chunk size and grid of the current configuration."""
         n, c, g = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
         _check(_lib.fea_batch_info(self.handle, ctypes.byref(n), ctypes.byref(c), ctypes.byref(g)))
         return dict(items=n.value, chunk=c.value, grid=g.value)
 
     def autotune(self, reps: int = 3, stream=None):
+        """Time chunk sizes and grids, keep the fastest; returns it."""
         c, g, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
         _check(_lib.fea_batch_autotune(self.handle, reps, _stream(stream), ctypes.byref(c), ctypes.byref(g),
                                        ctypes.byref(ms)))
         return dict(chunk=c.value, grid=g.value, ms=ms.value)
 
     def capture(self, stream=None):
+        """Capture one assembly as a CUDA graph; later assemble() calls replay it."""
         _check(_lib.fea_batch_capture(self.handle, _stream(stream)))
 
     def assemble(self, stream=None):
+        """Assemble every system of the batch (overwrite)."""
         _check(_lib.fea_batch_assemble(self.handle, _stream(stream)))
 
     def latency_ns(self, stream=None):
-        import numpy as np
+        """Per-mesh latency of the last assembly, ns (uint64 numpy)."""
         out = np.zeros(len(self.systems), dtype=np.uint64)
         _check(_lib.fea_batch_latency(self.handle, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
         return out
 
     def close(self):
+        """Destroy the batch handle."""
         if self.handle:
             _check(_lib.fea_batch_destroy(self.handle))
             self.handle = None
@@ -422,16 +446,19 @@ def fea_spmv(h, ndof: int, row_ptr, A, x, y, glob=None, shared=None, stream=None
 
 
 def fea_element_loop(op: "fea_operator", h, stress=None, stream=None):
+    """The J2 Gauss-point update of every element, without a scatter (stress: float64 [n_elems, 8, 6] or None)."""
     _check(_lib.fea_element_loop(ctypes.byref(op), h, _dptr(stress), _stream(stream)))
 
 
 def fea_element_loop_grid(op: "fea_operator", h) -> int:
+    """CTAs of the persistent element loop of op on the mesh."""
     n = ctypes.c_int32()
     _check(_lib.fea_element_loop_grid(ctypes.byref(op), h, ctypes.byref(n)))
     return int(n.value)
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:
+    """Kernels one fea_assemble call with op launches on the mesh."""
     n = ctypes.c_int()
     _check(_lib.fea_assemble_launches(ctypes.byref(op), h, ctypes.byref(n)))
     return n.value
