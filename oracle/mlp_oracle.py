@@ -28,10 +28,12 @@ HID = 32
 
 
 def n_params(n_in: int) -> int:
+    """Length of the parameter vector for n_in features."""
     return HID * n_in + HID + HID * HID + HID + HID + 1
 
 
 def unpack(p, n_in):
+    """(W1, b1, W2, b2, w3, b3) views of the parameter vector, in FP64."""
     p = np.asarray(p, dtype=np.float64)
     k = 0
     W1 = p[k:k + HID * n_in].reshape(HID, n_in); k += HID * n_in
@@ -44,6 +46,7 @@ def unpack(p, n_in):
 
 
 def pack(W1, b1, W2, b2, w3, b3):
+    """The parameter vector of the six arrays, in their order."""
     return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, [b3]])
 
 
@@ -58,6 +61,7 @@ def xavier_init(n_in: int, seed: int = 6) -> np.ndarray:
 
 
 def fit_scaler(X, y):
+    """(x mean, x std, y mean, y std), population deviations; a zero deviation becomes 1."""
     X = np.asarray(X, dtype=np.float64); y = np.asarray(y, dtype=np.float64)
     xm = X.mean(axis=0); xs = X.std(axis=0)
     ym = y.mean(); ys = y.std()
@@ -106,6 +110,8 @@ def adam_step(p, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def train(p, n_in, X, y, epochs, lr, scaler=None):
+    """Full-batch Adam from p for `epochs` steps: (parameters, scaler, the
+    loss of every epoch before its update)."""
     scaler = scaler or fit_scaler(X, y)
     m = np.zeros_like(p); v = np.zeros_like(p)
     losses = []
@@ -117,6 +123,7 @@ def train(p, n_in, X, y, epochs, lr, scaler=None):
 
 
 def predict(p, n_in, scaler, X):
+    """Predictions in target units for the rows of X."""
     xm, xs, ym, ys = scaler
     out, _, _ = forward(p, n_in, (np.asarray(X, dtype=np.float64) - xm) / xs)
     return out * ys + ym
@@ -180,6 +187,7 @@ def element_features(mesh, U=None, state=None):
 
 
 def item_features(mesh, chunk=128, U=None, state=None):
+    """Per work item (runs of `chunk` elements of one type), the mean of its elements' features."""
     F = element_features(mesh, U, state)
     out = []
     for t, f, c in work_items(mesh, chunk):

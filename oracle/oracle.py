@@ -48,6 +48,7 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle (built on first use), with its C signatures declared."""
     global _lib
     with _lock:
         if _lib is None:
@@ -95,12 +96,14 @@ def _c(a, dtype):
 
 
 class InvertedElement(RuntimeError):
+    """det J <= 0 at a quadrature point (the element id, or -1 for a single element)."""
     def __init__(self, elem):
         super().__init__(f"element {elem} has detJ <= 0 at a quadrature point")
         self.elem = elem
 
 
 def op_params(op: int, **kw) -> np.ndarray:
+    """Operator parameters in the oracle's order: diffusion (k0, k2, f); elasticity (E, nu, f_x, f_y, f_z)."""
     if op == OP_DIFFUSION:
         return np.array([kw.get("k0", 1.0), kw.get("k2", 0.0), kw.get("source", 1.0)], dtype=np.float64)
     f = kw.get("body_force", (1.0, 1.0, 1.0))
@@ -108,12 +111,14 @@ def op_params(op: int, **kw) -> np.ndarray:
 
 
 def quadrature(etype: int, tet_rule: int = 1):
+    """Reference points [nq, 3] and weights [nq] of the element type's rule (tet_rule 0: centroid, 1: 4-point)."""
     pts = np.zeros((8, 3)); w = np.zeros(8)
     nq = lib().oracle_quadrature(etype, tet_rule, _ptr(pts), _ptr(w))
     return pts[:nq].copy(), w[:nq].copy()
 
 
 def shape(etype: int, p):
+    """N [nn] and dN/dxi [nn, 3] of the element type at reference point p."""
     p = _c(p, np.float64)
     N = np.zeros(8); dN = np.zeros((8, 3))
     nn = lib().oracle_shape(etype, _ptr(p), _ptr(N), _ptr(dN))
@@ -226,7 +231,7 @@ def assemble_rows(mesh, nodes, op: int = OP_DIFFUSION, tet_rule: int = 1, max_co
 # ---------------------------------------------------------------------------
 
 class NoConvergence(RuntimeError):
-    pass
+    """The return map needed more than max_iter Newton updates."""
 
 
 J2_DEFAULTS = dict(young=1.0, poisson=0.3, sigma0=1e-3, sigma_inf=3e-3, delta=300.0, hardening=1e-2,
