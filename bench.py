@@ -143,6 +143,7 @@ def variant_operators(fea) -> dict:
 
 
 def hex_cube_mesh(n=128):
+    """The headline workload's mesh: n^3 hex8 cube, interior nodes jittered by +-0.2h (PCG64 seed 2)."""
     from paper_1805_03949_gb300 import meshgen as mg
     return mg.hex_cube(n, 0.2, 2)
 
@@ -217,6 +218,9 @@ def whole_job_rate(units_per_rank, world, ms):
 # ---------------------------------------------------------------------------
 
 def run_ours(args, rank, world, local_rank):
+    """The engine's arm: every assembly variant, the product and the finite-strain operator
+    on one replica per rank, the end-to-end pipeline, then the headline JSON line on
+    rank 0."""
     import torch
     from paper_1805_03949_gb300 import fea
 
@@ -649,6 +653,7 @@ def workload_batch(dev, steps=10):
 
 
 def other_workloads(args, dev):
+    """Time the mixed-element diffusion, J2 and batch workloads named in --workloads."""
     out = {}
     wanted = [c for c in args.workloads.split(",") if c]
     for key, fn in (("hybrid", workload_hybrid), ("j2", workload_j2), ("batch", workload_batch)):
@@ -675,6 +680,7 @@ def _slab(mesh, layers, n):
 
 
 def cpu_baseline(args, mesh=None, layers=None):
+    """The FP64 oracle, as it stands, on the first `layers` cell layers of the workload (one thread)."""
     from oracle import oracle as O
     n = args.n
     mesh = mesh if mesh is not None else hex_cube_mesh(n)
@@ -700,6 +706,7 @@ def workload_name(n: int) -> str:
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle timed on slabs of the workload (rank 0 only)."""
     if rank != 0:
         return
     mesh = hex_cube_mesh(args.n)
@@ -725,6 +732,7 @@ def run_reference(args, rank, world):
 
 
 def make_parser() -> argparse.ArgumentParser:
+    """Command-line options of both arms."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -746,6 +754,7 @@ def make_parser() -> argparse.ArgumentParser:
 
 
 def main():
+    """Run the arm --impl selects and print its JSON line."""
     ap = make_parser()
     args = ap.parse_args()
     unknown = sorted({v for v in args.only.split(",") if v} - set(VARIANTS))
