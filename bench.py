@@ -524,7 +524,7 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, 
     cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, and
     the same queues with stealing as the fallback once a CTA's own queue is empty."""
     import torch
-    from oracle import mlp_oracle
+    from paper_1805_03949_gb300 import meshgen as mg
     run = run or s.assemble
     grid_fn = grid_fn or fea.fea_persistent_grid
     item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
@@ -532,7 +532,7 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, 
     out = {"persistent_steal": _time_calls(lambda: run(steal), steps)}
     s.check()
     y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
-    h = fea.fea_costmodel_create(6, mlp_oracle.xavier_init(6).astype(np.float32))
+    h = fea.fea_costmodel_create(6, mg.mlp_initial_params(6).astype(np.float32))
     t0 = time.perf_counter()
     fea.fea_costmodel_fit_scaler(h, X, y)
     loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())

@@ -50,16 +50,6 @@ def pack(W1, b1, W2, b2, w3, b3):
     return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, [b3]])
 
 
-def xavier_init(n_in: int, seed: int = 6) -> np.ndarray:
-    """Xavier-uniform weights (bound sqrt(6 / (fan_in + fan_out))), zero biases, PCG64(seed)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    lim = lambda fi, fo: np.sqrt(6.0 / (fi + fo))
-    W1 = rng.uniform(-lim(n_in, HID), lim(n_in, HID), (HID, n_in))
-    W2 = rng.uniform(-lim(HID, HID), lim(HID, HID), (HID, HID))
-    w3 = rng.uniform(-lim(HID, 1), lim(HID, 1), HID)
-    return pack(W1, np.zeros(HID), W2, np.zeros(HID), w3, 0.0)
-
-
 def fit_scaler(X, y):
     """(x mean, x std, y mean, y std), population deviations; a zero deviation becomes 1."""
     X = np.asarray(X, dtype=np.float64); y = np.asarray(y, dtype=np.float64)

@@ -19,6 +19,7 @@ problems:
 * ``batch_meshes(count, seed)`` -- many tet4/hex8 boxes of log-uniform size
 * ``fourier_displacement(...)`` -- smooth nodal displacement field (sum of
   sine modes) used as the state of the elastoplastic operator
+* ``mlp_initial_params(n_in, seed)`` -- seeded initial weights of the cost model
 
 Element type codes and local node orders (shared convention of the C-ABI):
 
@@ -384,3 +385,20 @@ def partition_elements(mesh: Mesh, parts: int):
         sub = Mesh(mesh.coords[glob].copy(), mesh.types[ids].copy(), coff, lconn, dict(mesh.meta, part_of=len(out)))
         out.append((sub, glob))
     return out, mult
+
+
+def mlp_initial_params(n_in: int, seed: int = 6, hidden: int = 32) -> np.ndarray:
+    """Initial parameters of the cost model (n_in -> hidden tanh -> hidden tanh
+    -> 1), in the C-ABI's order W1 [hidden][n_in], b1, W2 [hidden][hidden], b2,
+    w3 [hidden], b3: Xavier-uniform weights (bound sqrt(6 / (fan_in +
+    fan_out))) drawn from PCG64(seed) in that order, zero biases.  A seeded
+    input like the meshes, for the engine and the oracle alike."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def lim(fan_in, fan_out):
+        return np.sqrt(6.0 / (fan_in + fan_out))
+
+    W1 = rng.uniform(-lim(n_in, hidden), lim(n_in, hidden), (hidden, n_in))
+    W2 = rng.uniform(-lim(hidden, hidden), lim(hidden, hidden), (hidden, hidden))
+    w3 = rng.uniform(-lim(hidden, 1), lim(hidden, 1), hidden)
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), w3, [0.0]])

@@ -31,7 +31,7 @@ def _tensors(X, y):
 def test_scaler_gradient_and_loss_match_oracle(n):
     fea = engine()
     X, y = _data(n)
-    p0 = M.xavier_init(6).astype(np.float32)
+    p0 = mg.mlp_initial_params(6).astype(np.float32)
     p0 = p0 + np.random.default_rng(2).normal(0, 0.05, p0.shape).astype(np.float32)
     h = fea.fea_costmodel_create(6, p0)
     try:
@@ -57,7 +57,7 @@ def test_adam_steps_and_inference_match_oracle():
     import torch
     fea = engine()
     X, y = _data(3000, seed=5)
-    p0 = M.xavier_init(6).astype(np.float32)
+    p0 = mg.mlp_initial_params(6).astype(np.float32)
     h = fea.fea_costmodel_create(6, p0)
     try:
         Xd, yd = _tensors(X, y)
@@ -137,7 +137,7 @@ def _study(fea, s, base, chunk, Xkw, capsys, label):
     res = {"steal": _time_assemble(s, steal)}
     X = fea.fea_item_features(s.handle, chunk, len(counts), **Xkw)
     y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device="cuda", dtype=torch.float32))
-    h = fea.fea_costmodel_create(6, M.xavier_init(6).astype(np.float32))
+    h = fea.fea_costmodel_create(6, mg.mlp_initial_params(6).astype(np.float32))
     try:
         fea.fea_costmodel_fit_scaler(h, X, y)
         loss = float(fea.fea_costmodel_train(h, X, y, 600, 1e-2).item())

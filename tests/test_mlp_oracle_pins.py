@@ -19,7 +19,7 @@ def _data(n=200, n_in=6, seed=1):
 
 def test_parameter_count_and_layout():
     assert M.n_params(6) == 1313
-    p = M.xavier_init(6)
+    p = mg.mlp_initial_params(6)
     parts = M.unpack(p, 6)
     assert [np.size(x) for x in parts] == [192, 32, 1024, 32, 32, 1]
     np.testing.assert_array_equal(M.pack(*parts), p)
@@ -50,7 +50,7 @@ def test_forward_closed_form():
 
 def test_gradient_matches_central_differences():
     X, y = _data(60)
-    p = M.xavier_init(6) + np.random.default_rng(3).normal(size=1313) * 0.05
+    p = mg.mlp_initial_params(6) + np.random.default_rng(3).normal(size=1313) * 0.05
     sc = M.fit_scaler(X, y)
     _, g = M.loss_grad(p, 6, X, y, sc)
     rng = np.random.default_rng(4)
@@ -71,7 +71,7 @@ def test_first_adam_step_is_minus_lr_sign():
 
 def test_training_decreases_the_loss():
     X, y = _data(300)
-    p0 = M.xavier_init(6)
+    p0 = mg.mlp_initial_params(6)
     _, sc, losses = M.train(p0, 6, X, y, 200, 1e-2)
     assert losses[-1] < 0.2 * losses[0]
 
