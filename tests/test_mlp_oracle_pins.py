@@ -48,6 +48,21 @@ def test_forward_closed_form():
     np.testing.assert_allclose(H1, np.tile(np.tanh(b1), (5, 1)), rtol=1e-15)
 
 
+def test_predict_undoes_the_standardisation():
+    """On the training data, the mean squared error of the predictions in
+    target units is the standardised loss times the target variance, and a
+    network whose last layer is zero predicts the target mean."""
+    X, y = _data()
+    sc = M.fit_scaler(X, y)
+    p = mg.mlp_initial_params(6, seed=8)
+    loss, _ = M.loss_grad(p, 6, X, y, sc)
+    pred = M.predict(p, 6, sc, X)
+    assert np.mean((pred - y) ** 2) == pytest.approx(loss * sc[3] ** 2, rel=1e-12)
+    W1, b1, W2, b2, w3, b3 = M.unpack(p, 6)
+    zero = M.pack(W1, b1, W2, b2, np.zeros_like(w3), 0.0)
+    np.testing.assert_allclose(M.predict(zero, 6, sc, X), np.full(len(y), y.mean()), rtol=1e-14)
+
+
 def test_gradient_matches_central_differences():
     X, y = _data(60)
     p = mg.mlp_initial_params(6) + np.random.default_rng(3).normal(size=1313) * 0.05
