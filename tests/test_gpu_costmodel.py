@@ -106,8 +106,10 @@ def test_item_features_match_oracle():
         s.close()
 
 
-def _time_assemble(s, op, reps=7):
+def _time_assemble(s, op, reps=15):
+    """Median of `reps` CUDA-event timings after one untimed call."""
     import torch
+    s.assemble(op)
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
