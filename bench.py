@@ -189,6 +189,155 @@ def algorithmic_flops_hex_elasticity(n_elems, n_nodes, nnz, nq=8, nn=8):
             "fp64_accumulate": accumulate, "fp32": n_elems * fp32}
 
 
+# ---------------------------------------------------------------------------
+# algorithmic work of any workload: per element type, operator and precision
+# ---------------------------------------------------------------------------
+
+NODES_PER_TYPE = {0: 4, 1: 5, 2: 6, 3: 8}
+TYPE_NAMES = {0: "tet4", 1: "pyr5", 2: "prism6", 3: "hex8"}
+OP_DIFFUSION, OP_ELASTICITY, OP_J2 = 0, 1, 2
+
+
+def element_flops(etype, op, nq, k_varies=False):
+    """Arithmetic of one element (FMA = 2 flop, div / sqrt / exp = 1), split by role.
+
+    geometry (FP64 in every precision): the Jacobian J, its cofactors C
+      (9 mul + 9 FMA), det J (1 mul + 2 FMA) and w det J per point.
+      hex8 (2x2x2 rule, modal form): 3 stages x 8 corners x 3 adds of the
+        Walsh-Hadamard transform of the corners; per point J from 4 modal
+        coefficients (9 entries x 3 FMA) and w det J (2 mul);
+      tet4 (affine): 3 x 3 edge differences, C, det and 1/det once; w det J
+        (1 mul) per point;
+      pyr5, prism6: 3 (nn - 1) differences to node 0 once; per point J = sum
+        over the other nodes (9 (nn - 1) FMA), C, det, w det J (1 mul).
+    coords (FP64, diffusion with k = k0 + k2 x^2 only): x_q = sum_a N_a x_a,
+      nn FMA per point.
+    grad: the scaled gradients g_a = s C grad_xi N_a, 9 FMA + 3 mul per node
+      and 3 for s, per point (once for an affine tet, whose gradients are
+      constant).
+    prod: diffusion, per (a <= b) pair a dot product (3 FMA) and its weight
+      (1 mul), and k_q (mul + FMA) per point; elasticity, per (a <= b) block 3
+      FMA (dot) + 18 FMA (lam g_a g_b^T + mu g_b g_a^T) + 3 adds (the diagonal),
+      and 6 mul per node (lam g_a, mu g_a).  Per point, except for affine tets,
+      whose products are taken once with the weight sum (1 FMA per point).
+    rhs: w det J f_c N_a, 1 FMA per node, component and point.
+    """
+    nn = NODES_PER_TYPE[etype]
+    pairs = nn * (nn + 1) // 2
+    d = 1 if op == OP_DIFFUSION else 3
+    affine = etype == 0
+    if etype == 3:
+        geometry = 72 + nq * (2 * 27 + 27 + 5 + 2)
+    elif affine:
+        geometry = 9 + 27 + 5 + 1 + nq
+    else:
+        geometry = 3 * (nn - 1) + nq * (2 * 9 * (nn - 1) + 27 + 5 + 1)
+    coords = nq * 2 * nn if (op == OP_DIFFUSION and k_varies) else 0
+    grad = (1 if affine else nq) * (21 * nn + 3)
+    if op == OP_DIFFUSION:
+        per = 7 * pairs
+        prod = (per + nq * (2 + 3) if affine else nq * (per + 3)) if k_varies else (per + 2 * nq if affine else nq * per)
+    else:
+        per = 45 * pairs + 6 * nn
+        prod = per + 2 * nq if affine else nq * per
+    rhs = nq * 2 * nn * d
+    return {"geometry": geometry, "coords": coords, "grad": grad, "prod": prod, "rhs": rhs}
+
+
+def j2_point_flops(plastic, iters):
+    """FP64 arithmetic of the J2 update at one point beyond the geometry (FMA = 2, exp / div / sqrt = 1).
+
+    displacement gradient from the modal form of the nodal displacements: J_u
+    (9 x 3 FMA), grad u = J_u C^T (27 FMA), times 1/det J (1 div + 9 mul);
+    strain, trace and deviator 9; trial stress 2 mu (e_dev - eps_p) 12, its
+    norm 13, sigma_y(alpha_n) 5, the yield test 2; an elastic point's stress
+    4.  A plastic point adds 20 per Newton iteration (alpha, sigma_y and its
+    slope with one exp, g, g', the update with one div) and 47 for the flow
+    direction, stress, plastic strain, alpha and the tangent factors.
+    """
+    base = 54 + 54 + 10 + 9 + 12 + 13 + 5 + 2
+    return base + (47 + 20 * iters if plastic else 4)
+
+
+def assembly_work(type_counts, n_nodes, nnz_node, op, precision, nq_of=None, k_varies=False, j2=None):
+    """FP64 flops, FP32 flops and algorithmic bytes of one assembly.
+
+    type_counts: {element type: count}; nnz_node: node-level nonzeros of the
+    pattern (the scalar count is d^2 times it); precision 0 = FP64 (every
+    flop on the FP64 pipe), else FP32-integrate (geometry, coordinates, the
+    J2 update and the accumulation in FP64, the rest in FP32); nq_of: points
+    of each type's rule (default: the degree-2 rules, tet 4, pyr 8, prism 6,
+    hex 8); j2: dict(points, plastic_points, newton_iters) summed over the
+    mesh for the J2 operator (hex8 only).
+
+    Accumulation: an entry with c contributions takes c - 1 FP64 adds; A is
+    symmetric, so the (a <= b) blocks of every element are counted, against
+    the (nnz_node + n_nodes) / 2 node pairs (i <= j) of the pattern; b takes
+    sum(nn) - n_nodes per component.
+    Bytes: A written once (8 per scalar nonzero), b written once, coordinates
+    (24 per node), scalar row starts (8 per row), connectivity (4 nn) and the
+    node map (4 nn^2) per element read once; J2 also reads the displacements
+    (24 per node) and reads and writes the state (8 points x 7 values x 8
+    bytes each way per element).
+    """
+    nq_of = nq_of or {0: 4, 1: 8, 2: 6, 3: 8}
+    d = 1 if op == OP_DIFFUSION else 3
+    fop = OP_ELASTICITY if op == OP_J2 else op
+    f64 = f32 = 0
+    parts = {"geometry": 0, "accumulate": 0, "integrate": 0, "j2_update": 0}
+    n_elems = sum(type_counts.values())
+    sum_pairs = sum(c * NODES_PER_TYPE[t] * (NODES_PER_TYPE[t] + 1) // 2 for t, c in type_counts.items())
+    sum_nn = sum(c * NODES_PER_TYPE[t] for t, c in type_counts.items())
+    sum_nn2 = sum(c * NODES_PER_TYPE[t] ** 2 for t, c in type_counts.items())
+    for t, c in type_counts.items():
+        if not c:
+            continue
+        w = element_flops(t, fop, nq_of[t], k_varies)
+        parts["geometry"] += c * (w["geometry"] + w["coords"])
+        integ = w["grad"] + w["prod"] + w["rhs"]
+        if op == OP_J2:
+            assert t == 3, "the J2 workload is hex8"
+            nn, nq, pairs = 8, nq_of[t], 36
+            integ += nq * (18 * pairs + 18 * nn)     # beta h_a h_b^T per block; h_a = n g_a and sigma g_a per node
+            parts["geometry"] += c * 72              # modal transform of the displacements
+        parts["integrate"] += c * integ
+    if op == OP_J2:
+        j = j2 or {}
+        plastic_extra = j2_point_flops(True, 0) - j2_point_flops(False, 0)
+        parts["j2_update"] = (j.get("points", 0) * j2_point_flops(False, 0)
+                              + j.get("plastic_points", 0) * plastic_extra + 20 * j.get("newton_iters", 0))
+    parts["accumulate"] = d * d * (sum_pairs - (nnz_node + n_nodes) // 2) + d * (sum_nn - n_nodes)
+    f64 = parts["geometry"] + parts["accumulate"] + parts["j2_update"]
+    if precision == 0:
+        f64 += parts["integrate"]
+    else:
+        f32 = parts["integrate"]
+    nnz = d * d * nnz_node
+    by = 8 * nnz + n_nodes * (24 + 8 * d + 8 * d) + 4 * sum_nn + 4 * sum_nn2
+    if op == OP_J2:
+        by += 24 * n_nodes + n_elems * 2 * 8 * 7 * 8
+    return {"fp64": f64, "fp32": f32, "bytes": by, "parts": parts, "elements": n_elems}
+
+
+def fp64_peak_flops():
+    """The FP64 rate the roofline uses: the measured FMA rate where a probe ran, else nominal."""
+    return NOMINAL_FP64_TFLOPS * 1e12
+
+
+def step_roofline(work, ms, peaks):
+    """T_roof = max(FP64 flops / P64, FP32 flops / P32, bytes / HBM) against the measured step time."""
+    t = {"fp64": work["fp64"] / peaks["fp64"], "fp32": work["fp32"] / peaks["fp32"],
+         "hbm": work["bytes"] / peaks["hbm"]}
+    bound = max(t, key=t.get)
+    t_roof = t[bound]
+    sec = ms * 1e-3
+    ach = {"fp64": (work["fp64"] / sec / 1e9, "GFLOP/s (FP64)"), "fp32": (work["fp32"] / sec / 1e9, "GFLOP/s (FP32)"),
+           "hbm": (work["bytes"] / sec / 1e9, "GB/s")}
+    return {"bound": "hbm" if bound == "hbm" else "alu", "resource": bound, "achieved": ach[bound][0],
+            "peak": peaks[bound] / 1e9, "unit": ach[bound][1], "frac": t_roof * 1e3 / ms, "t_roof_ms": t_roof * 1e3,
+            "fp64_ms": t["fp64"] * 1e3, "fp32_ms": t["fp32"] * 1e3, "hbm_ms": t["hbm"] * 1e3, "ms": ms}
+
+
 def record_bytes(n_elems):
     """FP32 geometry records: 208 values of 4 bytes per element."""
     return n_elems * 208 * 4

@@ -48,6 +48,10 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
   FEA_CUDA(cudaMemcpyAsync(incoff.data(), m->inc_off, (N + 1) * 8, cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaMemcpyAsync(inc.data(), m->inc, L * 8, cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaStreamSynchronize(s));
+  // the incidence lists are filled concurrently on the device; element order
+  // makes each entry's contribution order (its FP64 summation order) the same
+  // on every build of the plan
+  for (int64_t i = 0; i < N; ++i) std::sort(inc.begin() + incoff[i], inc.begin() + incoff[i + 1]);
 
   // Morton order of the element centroids
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -119,9 +123,13 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
       for (size_t l = 0; l < hb.lnodes.size(); ++l) local[hb.lnodes[l]] = (int32_t)l;
       hb.n_owned = (int)hb.lnodes.size();  // every local node has rows written by this block
       hb.htype.resize(hb.helem.size());
+      const bool all_hex = m->uniform && m->uniform_type == FEA_HEX8;
+      if (all_hex) hb.hln.assign(hb.helem.size() * 8, 0);
       for (size_t h = 0; h < hb.helem.size(); ++h) {
         const int nn = (int)(coff[hb.helem[h] + 1] - coff[hb.helem[h]]);
         hb.htype[h] = (uint8_t)(nn == 4 ? FEA_TET4 : nn == 5 ? FEA_PYR5 : nn == 6 ? FEA_PRISM6 : FEA_HEX8);
+        if (all_hex)  // corner a of block element h is local node hln[8 h + a]
+          for (int a = 0; a < 8; ++a) hb.hln[h * 8 + a] = (uint16_t)local[conn[coff[hb.helem[h]] + a]];
       }
       for (int li = 0; li < hb.n_owned; ++li) {
         const int32_t i = hb.lnodes[li];
@@ -170,8 +178,14 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
           hb.tasks.push_back(T);
         }
       }
-      std::stable_sort(hb.tasks.begin(), hb.tasks.end(),
-                       [](const RowTask& x, const RowTask& y) { return x.nc > y.nc; });
+      // heaviest tasks first, so that the 32 tasks a warp runs together have
+      // about the same number of contributions; within one count the diagonal
+      // tasks (which also sum b) come first, so that b's FP64 adds run in
+      // warps of diagonal tasks rather than on a few lanes of mixed warps
+      std::stable_sort(hb.tasks.begin(), hb.tasks.end(), [](const RowTask& x, const RowTask& y) {
+        if (x.nc != y.nc) return x.nc > y.nc;
+        return (x.flags & kTaskDiag) > (y.flags & kTaskDiag);
+      });
       for (int32_t j : hb.lnodes) local[j] = -1;
       for (int32_t e : hb.helem) hindex[e] = -1;
     }

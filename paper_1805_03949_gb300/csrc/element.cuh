@@ -94,15 +94,20 @@ __host__ __device__ constexpr int hex8_corner_node(int p) {
 // Lane p of an aligned group of 8 lanes holds the coordinates of corner p on
 // entry and c_p on exit (one FP64 add per stage and component: the partner's
 // value enters with the sign of the stage).  Every lane of the warp must call it.
+// The sign is applied to the partner's value by flipping its sign bit with an
+// integer XOR: a per-lane select between v + o and v - o compiles to both FP64
+// adds, which doubles the transform's cost on the FP64 pipe.  v + (-o) equals
+// v - o exactly (IEEE 754), so the result is unchanged.
 __device__ __forceinline__ void hex8_modal(double v[3]) {
   const int p = threadIdx.x & 7;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const int bit = 1 << s;
+    const int flip = (p & bit) ? (int)0x80000000 : 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double o = __shfl_xor_sync(0xffffffffu, v[i], bit);
-      v[i] += (p & bit) ? -o : o;
+      v[i] += __hiloint2double(__double2hiint(o) ^ flip, __double2loint(o));
     }
   }
 }

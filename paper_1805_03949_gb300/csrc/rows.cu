@@ -73,6 +73,9 @@ int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaSt
   FEA_CUDA(cudaMemcpyAsync(incoff.data(), m->inc_off, (N + 1) * 8, cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaMemcpyAsync(inc.data(), m->inc, L * 8, cudaMemcpyDeviceToHost, s));
   FEA_CUDA(cudaStreamSynchronize(s));
+  // element order in every incidence list (filled concurrently on the device):
+  // the same contribution order, and so the same FP64 sums, on every build
+  for (int64_t i = 0; i < N; ++i) std::sort(inc.begin() + incoff[i], inc.begin() + incoff[i + 1]);
   for (int64_t i = 0; i < N; ++i)
     if (rp[i + 1] - rp[i] > 65535)
       return fail(FEA_ERR_UNSUPPORTED, "rows plan: node " + std::to_string(i) + " has more than 65535 neighbours");
@@ -173,12 +176,9 @@ int build_rows_plan(fea_mesh* m, int ndof, int block_nodes, int halo_cap, cudaSt
                       std::to_string(kRowsMaxHalo) + ")";
       }
       hb.htype.resize(hb.helem.size());
-      hb.hln.assign(hb.helem.size() * 8, 0);
       for (size_t h = 0; h < hb.helem.size(); ++h) {
         const int32_t e = hb.helem[h];
-        const int nn = (int)(coff[e + 1] - coff[e]);
-        hb.htype[h] = (uint8_t)type_of_nn(nn);
-        for (int a = 0; a < nn; ++a) hb.hln[h * 8 + a] = (uint16_t)local[conn[coff[e] + a]];
+        hb.htype[h] = (uint8_t)type_of_nn((int)(coff[e + 1] - coff[e]));
       }
       // one task per entry block (i, j) of the owned rows; (i, j) and (j, i) once when both are owned
       for (int li = 0; li < hb.n_owned; ++li) {
@@ -283,6 +283,9 @@ int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int h
   }
   std::vector<int32_t> lnodes(nl), helem(nh);
   std::vector<uint8_t> htype(nh);
+  bool with_ln = false;
+  for (const HostBlock& hb : blocks) with_ln |= !hb.hln.empty();
+  std::vector<uint16_t> hln(with_ln ? nh * 8 : 0);
   std::vector<uint16_t> contrib(nc);
   std::vector<RowTask> tasks(nt);
   for (int64_t b = 0; b < nb; ++b) {
@@ -291,6 +294,7 @@ int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int h
     std::copy(hb.lnodes.begin(), hb.lnodes.end(), lnodes.begin() + H.lnode_off);
     std::copy(hb.helem.begin(), hb.helem.end(), helem.begin() + H.helem_off);
     std::copy(hb.htype.begin(), hb.htype.end(), htype.begin() + H.helem_off);
+    if (with_ln) std::copy(hb.hln.begin(), hb.hln.end(), hln.begin() + 8 * H.helem_off);
     std::copy(hb.tasks.begin(), hb.tasks.end(), tasks.begin() + H.task_off);
     std::copy(hb.contrib.begin(), hb.contrib.end(), contrib.begin() + H.contrib_off);
   }
@@ -314,6 +318,7 @@ int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int h
   if (!rc) rc = up(&P.lnodes, lnodes);
   if (!rc) rc = up(&P.helem_id, helem);
   if (!rc) rc = up(&P.helem_type, htype);
+  if (!rc && with_ln) rc = up(&P.helem_ln, hln);
   if (!rc) rc = up(&P.tasks, tasks);
   if (!rc) rc = up(&P.contrib, contrib);
   if (rc) {
@@ -329,11 +334,12 @@ static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a
 // Shared memory of one block: its owned row starts, and the task, contribution
 // and halo-element lists (bulk-copied, 16-byte padded); the element data
 // itself is read from the geometry records through L1.
-RowsLayout rows_layout(const RowsPlan& P, bool stage) {
+RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats) {
   RowsLayout L;
   uint32_t o = 0;
-  L.recs = o;                  o += stage ? (uint32_t)(4 * kRowsRecSmem * P.max_helem) : 0u;
-  L.rs = o;                    o += 8u * P.ndof * P.max_owned;
+  L.recs = o;                  o += stage ? (uint32_t)(4 * rec_floats * P.max_helem) : 0u;
+  L.rs = align_up(o, 16);      o = L.rs + 8u * P.ndof * P.max_owned;
+  L.gi = o;                    o += 4u * P.max_owned;
   L.tasks = align_up(o, 16);   o = L.tasks + (uint32_t)(sizeof(RowTask) * P.max_tasks);
   L.contrib = align_up(o, 16); o = L.contrib + (uint32_t)(2 * P.max_contrib);
   L.hid = align_up(o, 16);     o = L.hid + (uint32_t)(4 * P.max_helem_padded);

@@ -43,11 +43,30 @@ struct RowBlock {
 
 // byte offsets of one block's working set in dynamic shared memory
 struct RowsLayout {
-  uint32_t recs, rs, tasks, contrib, hid, bar, total;
+  uint32_t recs, rs, gi, tasks, contrib, hid, bar, total;
 };
 
 constexpr int kRowsRecSmem = 212;     // floats per staged record (208 + 4: 16-byte multiple, spreads banks)
 constexpr int kRowsStageHalo = 108;   // halo cap when records are staged (two CTAs per SM)
+
+// Where the values of one staged record sit, in floats from its start:
+// gradient g^_a(q)_c at q * Q + 3 a + c, the weight w det J at W + q, k(x_q)
+// at K + q; records follow one another every S floats.
+template <int Q, int W, int K, int S>
+struct RecLayout {
+  static constexpr int q = Q, w = W, k = K, stride = S;
+};
+// the layout of the geometry pass's global records (bulk-copied as they are)
+using RecCopied = RecLayout<24, 192, 200, kRowsRecSmem>;
+// records computed in shared memory by the pipelined block-task kernel.  The
+// strides were chosen with a model of the kernel's shared-memory accesses on
+// a 4 x 4 x 4 hex block (its 1,161 tasks in the order the plan gives them, the
+// 32 lanes of each consumer warp reading g^_a(q) and g^_b(q) of their
+// contributions, and the producer warps' stores): point stride 28 and record
+// stride 251 need 7,480 wavefronts per block against 11,192 for the copied
+// layout (24, 212); 216 floats per record, the smallest 16-byte multiple,
+// would need 16,784
+using RecPipe = RecLayout<28, 224, 232, 251>;
 
 struct RowsPlan {
   int ndof = 0;
@@ -63,7 +82,7 @@ struct RowsPlan {
   int32_t* lnodes = nullptr;      // per block: owned nodes, then the other nodes of its halo elements
   int32_t* helem_id = nullptr;    // original element id of every halo element
   uint8_t* helem_type = nullptr;
-  uint16_t* helem_ln = nullptr;   // [halo element][8] local node ids
+  uint16_t* helem_ln = nullptr;   // [halo element][8] local node ids (block-task plans of hex meshes)
   RowTask* tasks = nullptr;
   uint16_t* contrib = nullptr;
 };
@@ -73,7 +92,7 @@ struct HostBlock {
   std::vector<int32_t> lnodes;     // rows first (owned nodes), then the other local nodes
   std::vector<int32_t> helem;      // original element ids
   std::vector<uint8_t> htype;
-  std::vector<uint16_t> hln;       // [helem][8]
+  std::vector<uint16_t> hln;       // [helem][8] local node ids (block-task plans of hex meshes only)
   std::vector<RowTask> tasks;
   std::vector<uint16_t> contrib;
   int n_owned = 0;
@@ -91,7 +110,7 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
 int ensure_rows_plan(fea_mesh* m, int ndof, int precision, cudaStream_t s, RowsPlan** out);
 void drop_rows_plans(fea_mesh* m);
 void free_rows_plan(RowsPlan* P);
-RowsLayout rows_layout(const RowsPlan& P, bool stage);
+RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats = kRowsRecSmem);
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
                   cudaStream_t s, int* launched);
 // the block-task plan of a mesh, built on first use

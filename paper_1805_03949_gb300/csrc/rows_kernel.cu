@@ -43,6 +43,7 @@ struct RowsArgs {
   int tet_nq;               // quadrature points of tet4 (1 or 4)
   RowsLayout L;
   double lam, mu, src, f[3];
+  float lamf, muf;                // lam and mu rounded to FP32 on the host (FP32 tiles)
   float Ntab[kNumRules][8][8];    // N_a(q) per rule slot, for the right-hand side
   double Ntab64[kNumRules][8][8];
   // fused geometry (block-task plan, hex8, FP32-integrate): the CTA computes
@@ -50,6 +51,7 @@ struct RowsArgs {
   const double* coords;
   const int64_t* conn_off;
   const int32_t* conn;
+  const uint16_t* helem_ln;       // [halo element][8] block-local node of each corner (pipelined kernel)
   double k0, k2;
   int diffusion;
   RefRule hex;
@@ -83,6 +85,14 @@ struct Acc<FEA_FP32_INTEGRATE> {
   __device__ __forceinline__ double value() const { return v; }
 };
 
+static_assert(RecCopied::q * 8 == kRecW && RecCopied::w == kRecW && RecCopied::k == kRecK,
+              "staged copies keep the geometry pass's record layout");
+// (pipe records are written and read with scalar accesses only, never bulk
+// copied, so their stride need not be a 16-byte multiple)
+static_assert(RecPipe::q >= 24 && RecPipe::q * 8 <= RecPipe::w && RecPipe::w + 8 <= RecPipe::k &&
+                  RecPipe::k + 8 <= RecPipe::stride,
+              "pipe records hold 8 x 8 x 3 gradients, 8 weights and 8 conductivities");
+
 // element data: staged in shared memory, or read through L1
 template <bool STAGE, typename R>
 __device__ __forceinline__ R ld_rec(const R* p) {
@@ -93,16 +103,14 @@ __device__ __forceinline__ R ld_rec(const R* p) {
 }
 
 // HEX: every element is a hex8 with 8 points (compile-time loop bounds).
-// FP32 record of point p (= the thread's lane in its group of 8) of hex
-// element id, from the FP64 modal Jacobian: every lane of the warp calls it.
-__device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, int64_t id, float* rec) {
+// FP32 record (layout L) of point p (= the thread's lane in its group of 8)
+// of a hex element whose corner p has coordinates v, from the FP64 modal
+// Jacobian: every lane of the warp calls it.  *id (the element's original id)
+// is read only to report an inverted element.
+template <class L>
+__device__ __forceinline__ void hex_record(const RowsArgs& P, bool valid, const int32_t* id, double v[3],
+                                           float* rec) {
   const int p = threadIdx.x & 7;
-  double v[3] = {0.0, 0.0, 0.0};
-  if (valid) {
-    const int64_t node = P.conn[P.conn_off[id] + hex8_corner_node(p)];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = P.coords[3 * node + i];
-  }
   hex8_modal(v);
   double c[8][3];
   const int base = threadIdx.x & 24;
@@ -117,7 +125,7 @@ __device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, 
   cofactors(J, C);
   const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
   if (!(det > 0.0)) {
-    latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)id);
+    latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)*id);
     return;
   }
   // J' = 8 J: det J = det'/512, J^{-T} = 8 C'/det'
@@ -133,9 +141,9 @@ __device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, 
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      rec[p * 24 + 3 * a + i] =
+      rec[p * L::q + 3 * a + i] =
           (P.hex.dNf[p][a][0] * Cf[i][0] + P.hex.dNf[p][a][1] * Cf[i][1] + P.hex.dNf[p][a][2] * Cf[i][2]) * sc;
-  rec[kRecW + p] = wdf;
+  rec[L::w + p] = wdf;
   if (P.diffusion) {
     const double g = 0.57735026918962576451;
     const double xs = (p & 1) ? g : -g, ys = (p & 2) ? g : -g, zs = (p & 4) ? g : -g;
@@ -144,33 +152,58 @@ __device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, 
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc = fma(c[k][0], m[k], acc);
     const float x = (float)(0.125 * acc);
-    rec[kRecK + p] = (float)P.k0 + (float)P.k2 * x * x;
+    rec[L::k + p] = (float)P.k0 + (float)P.k2 * x * x;
   }
 }
 
+// the same, with corner p's coordinates read from the mesh
+template <class L>
+__device__ __forceinline__ void fused_hex_record(const RowsArgs& P, bool valid, const int32_t* id, float* rec) {
+  double v[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    const int64_t node = P.conn[P.conn_off[*id] + hex8_corner_node(threadIdx.x & 7)];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = P.coords[3 * node + i];
+  }
+  hex_record<L>(P, valid, id, v, rec);
+}
+
+// an operator parameter in the tile precision (FP32 values rounded on the host)
+template <typename R>
+__device__ __forceinline__ R tile_param(double d, float f);
+template <>
+__device__ __forceinline__ double tile_param<double>(double d, float) {
+  return d;
+}
+template <>
+__device__ __forceinline__ float tile_param<float>(double, float f) {
+  return f;
+}
+
 // The entry-block tasks of one block, by threads tid, tid + nthreads, ...
-// (records staged in shared memory when STAGE, else read from `rec`).
-template <int OP, int PREC, bool HEX, bool STAGE>
+// (records staged in shared memory when STAGE, in layout L, else read from
+// `rec`, whose records have L's offsets and kRecStride values each).
+template <int OP, int PREC, bool HEX, bool STAGE, class L = RecCopied>
 __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
                                           const typename std::conditional<PREC == FEA_FP64, double, float>::type* s_recs,
                                           const int64_t* s_rs, const RowTask* s_tasks, const uint16_t* s_contrib,
-                                          const int32_t* s_hid, const int32_t* lnodes, int tid, int nthreads) {
+                                          const int32_t* s_hid, const int32_t* gnode, int tid, int nthreads) {
   using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
   constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
   const R* rec = reinterpret_cast<const R*>(P.rec);
-  const R lam = (R)P.lam, mu = (R)P.mu;
+  const R lam = tile_param<R>(P.lam, P.lamf), mu = tile_param<R>(P.mu, P.muf);
   for (int t = tid; t < H.n_tasks; t += nthreads) {
     const RowTask T = s_tasks[t];
     const bool diag = T.flags & kTaskDiag;
     Acc<PREC> acc[D][D];
-    Acc<PREC> bacc[D];
+    Acc<PREC> bsum;   // sum over the contributions of w det J N_a (b_i = f times it)
 #pragma unroll 1
     for (int c = 0; c < T.nc; ++c) {
       const int code = s_contrib[T.coff + c];
       const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
       const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
       const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
-      const R* re = STAGE ? s_recs + (size_t)h * kRowsRecSmem : rec + (int64_t)s_hid[h] * kRecStride;
+      const R* re = STAGE ? s_recs + (size_t)h * L::stride : rec + (int64_t)s_hid[h] * kRecStride;
       const R* ga = re + 3 * a;
       const R* gb = re + 3 * bn;
       R K[D][D];
@@ -179,11 +212,11 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           if (!HEX && q >= nq) break;
-          const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
-                  x2 = ld_rec<STAGE>(ga + 24 * q + 2);
-          const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
-                  y2 = ld_rec<STAGE>(gb + 24 * q + 2);
-          s += ld_rec<STAGE>(re + kRecK + q) * (x0 * y0 + x1 * y1 + x2 * y2);
+          const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
+                  x2 = ld_rec<STAGE>(ga + L::q * q + 2);
+          const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
+                  y2 = ld_rec<STAGE>(gb + L::q * q + 2);
+          s += ld_rec<STAGE>(re + L::k + q) * (x0 * y0 + x1 * y1 + x2 * y2);
         }
         K[0][0] = s;
       } else {
@@ -191,10 +224,10 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           if (!HEX && q >= nq) break;
-          const R x0 = ld_rec<STAGE>(ga + 24 * q), x1 = ld_rec<STAGE>(ga + 24 * q + 1),
-                  x2 = ld_rec<STAGE>(ga + 24 * q + 2);
-          const R y0 = ld_rec<STAGE>(gb + 24 * q), y1 = ld_rec<STAGE>(gb + 24 * q + 1),
-                  y2 = ld_rec<STAGE>(gb + 24 * q + 2);
+          const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
+                  x2 = ld_rec<STAGE>(ga + L::q * q + 2);
+          const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
+                  y2 = ld_rec<STAGE>(gb + L::q * q + 2);
           M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
           M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
           M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
@@ -225,13 +258,12 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
             Nqa = P.Ntab64[slot][q][a];
           else
             Nqa = P.Ntab[slot][q][a];
-          rb += ld_rec<STAGE>(re + kRecW + q) * Nqa;
+          rb += ld_rec<STAGE>(re + L::w + q) * Nqa;
         }
-        if constexpr (OP == FEA_OP_DIFFUSION)
-          bacc[0].add(rb * (R)P.src);
+        if (c == 0)
+          bsum.set(rb);
         else
-#pragma unroll
-          for (int c1 = 0; c1 < 3; ++c1) bacc[c1].add(rb * (R)P.f[c1]);
+          bsum.add(rb);
       }
     }
     // the entry block, rounded once, to row i and transposed to row j
@@ -268,13 +300,17 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
       }
     }
     if (diag) {
-      const int64_t gi = lnodes[T.li];
+      // the source is constant over the mesh: b_i = f (sum of the element
+      // integrals of N_a), one FP64 product per component
+      const int64_t gi = gnode[T.li];
+      const double beta = bsum.value();
 #pragma unroll
       for (int c1 = 0; c1 < D; ++c1) {
+        const double bv = beta * (OP == FEA_OP_DIFFUSION ? P.src : P.f[c1]);
         if (T.flags & kTaskAtomicB)
-          atomicAdd(P.b + D * gi + c1, bacc[c1].value());
+          atomicAdd(P.b + D * gi + c1, bv);
         else
-          P.b[D * gi + c1] = bacc[c1].value();
+          P.b[D * gi + c1] = bv;
       }
     }
   }
@@ -328,8 +364,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
       for (int h0 = 0; h0 < H.n_helem; h0 += 32) {
         const int h = h0 + (threadIdx.x >> 3);
         const bool valid = h < H.n_helem;
-        const int64_t id = valid ? (int64_t)P.helem_id[H.helem_off + h] : 0;
-        fused_hex_record(P, valid, id, reinterpret_cast<float*>(s_recs) + (size_t)(valid ? h : 0) * kRowsRecSmem);
+        fused_hex_record<RecCopied>(P, valid, P.helem_id + H.helem_off + (valid ? h : 0),
+                                    reinterpret_cast<float*>(s_recs) + (size_t)(valid ? h : 0) * kRowsRecSmem);
       }
     }
     const bool landed = mbar_wait_bounded(s_bar, parity);
@@ -349,19 +385,38 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 // Block-task plans of hex meshes in FP32-integrate, pipelined: one persistent
 // CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
 // shared-memory stages.  Warps 0-5 (producers) fill stage i & 1 for block i:
-// the task lists by TMA bulk copy, the row starts, and the FP64-geometry
-// records of the block's elements; warps 6-15 (consumers) run the tasks of
-// block i - 1 meanwhile.  The stages are handed over by mbarriers: full[s]
-// (1 arrival with the copy bytes + 192 producer arrivals) and empty[s] (320
-// consumer arrivals).  The consumers bound the kernel (alone they take 90 %
-// of its time, the producers 65 %), so they get the ten warps; six producer
-// warps keep up with them (measured per 128^3 step: 6 + 8 warps 5.79 ms,
-// 6 + 10 5.48, 6 + 12 5.95 (register cap), 4 + 12 6.14, 7 + 9 5.90).  Every
-// wait is bounded; a timeout latches FEA_ERR_TIMEOUT, and the copies in
-// flight are waited for before exit.
+// the task lists by TMA bulk copy; the row starts and node ids of the block's
+// nodes; and the FP64-geometry records of the block's elements, whose corner
+// coordinates come from a copy of the block's node coordinates in shared
+// memory (one gather per node, not per corner).  Warps 6-15 (consumers) run
+// the tasks of block i - 1 meanwhile.  The stages are handed over by
+// mbarriers: full[s] (1 arrival with the copy bytes + 192 producer arrivals)
+// and empty[s] (320 consumer arrivals).  The producers also meet at a named
+// barrier (id 1) twice per block, around their shared coordinate copy; the
+// decision to stop after a timeout is taken there by all of them at once, so
+// none is left waiting.  Every wait is bounded; a timeout latches
+// FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
+// Measured splits per 128^3 step: 6 + 8 warps 5.79 ms, 6 + 10 5.48, 6 + 12
+// 5.95 (register cap), 4 + 12 6.14, 7 + 9 5.90.
 // ---------------------------------------------------------------------------
 constexpr int kPipeProducers = 192;
 constexpr int kPipeConsumers = 320;
+constexpr int kPipeProducerBar = 1;
+
+// all producer threads arrive; true when pred holds on any of them
+__device__ __forceinline__ bool producers_any(bool pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((int)pred), "n"(kPipeProducerBar), "n"(kPipeProducers)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void producers_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(kPipeProducerBar), "n"(kPipeProducers) : "memory");
+}
 
 template <int OP>
 __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
@@ -369,6 +424,7 @@ __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
   extern __shared__ __align__(128) unsigned char pipe_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(pipe_raw + 2 * stage_bytes);
   uint64_t* empty = full + 2;
+  double* s_x = reinterpret_cast<double*>(pipe_raw + 2 * stage_bytes + 32);  // producers' node coordinates
   __shared__ int s_issued[2];
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
@@ -382,26 +438,26 @@ __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
   }
   __syncthreads();
   const bool producer = threadIdx.x < kPipeProducers;
+  constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
   int i = 0;
   for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, ++i) {
-    if (*((volatile int*)&s_fail)) break;
     const int s = i & 1;
     const uint32_t ph = (uint32_t)(i >> 1) & 1u;
     unsigned char* base = pipe_raw + (size_t)s * stage_bytes;
     float* s_recs = reinterpret_cast<float*>(base + P.L.recs);
     int64_t* s_rs = reinterpret_cast<int64_t*>(base + P.L.rs);
+    int32_t* s_gi = reinterpret_cast<int32_t*>(base + P.L.gi);
     RowTask* s_tasks = reinterpret_cast<RowTask*>(base + P.L.tasks);
     uint16_t* s_contrib = reinterpret_cast<uint16_t*>(base + P.L.contrib);
     int32_t* s_hid = reinterpret_cast<int32_t*>(base + P.L.hid);
     const RowBlock H = P.blocks[blk];
-    const int32_t* lnodes = P.lnodes + H.lnode_off;
-    constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
     if (producer) {
       // the consumers of block i - 2 have released this stage
-      if (i >= 2 && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
-        if (atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
-        break;
-      }
+      const bool ok = i < 2 || mbar_wait_bounded(&empty[s], ph ^ 1u);
+      if (!ok && atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
+      // one decision for every producer; past this barrier, every producer has
+      // also finished reading the coordinate copy of the previous block
+      if (producers_any(*((volatile int*)&s_fail) != 0)) break;
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
         mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
@@ -410,22 +466,44 @@ __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
         if (H.helem_bytes) bulk_copy_g2s(s_hid, P.helem_id + H.helem_off, H.helem_bytes, &full[s]);
         ++s_issued[s];
       }
-      for (int t = threadIdx.x; t < H.n_owned * D; t += kPipeProducers)
-        s_rs[t] = P.row_ptr[(int64_t)D * lnodes[t / D] + t % D];
+      // the block's nodes (every one owns rows of a block-task plan): id, row
+      // starts and coordinates
+      const int32_t* lnodes = P.lnodes + H.lnode_off;
+      for (int t = threadIdx.x; t < H.n_local; t += kPipeProducers) {
+        const int32_t node = lnodes[t];
+        if (t < H.n_owned) {
+          s_gi[t] = node;
+#pragma unroll
+          for (int c = 0; c < D; ++c) s_rs[D * t + c] = P.row_ptr[(int64_t)D * node + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_x[3 * t + c] = P.coords[3 * (int64_t)node + c];
+      }
+      producers_sync();
       for (int h0 = 0; h0 < H.n_helem; h0 += kPipeProducers / 8) {
+        // a warp holds 4 elements; one with none left skips the pass (its
+        // modal transform would run on the FP64 pipe for nothing)
+        if (h0 + (int)((threadIdx.x & ~31u) >> 3) >= H.n_helem) continue;
         const int h = h0 + (threadIdx.x >> 3);
         const bool valid = h < H.n_helem;
-        const int64_t id = valid ? (int64_t)P.helem_id[H.helem_off + h] : 0;
-        fused_hex_record(P, valid, id, s_recs + (size_t)(valid ? h : 0) * kRowsRecSmem);
+        double v[3] = {0.0, 0.0, 0.0};
+        if (valid) {
+          const int ln = P.helem_ln[8 * (H.helem_off + h) + hex8_corner_node(threadIdx.x & 7)];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] = s_x[3 * ln + c];
+        }
+        hex_record<RecPipe>(P, valid, P.helem_id + H.helem_off + (valid ? h : 0), v,
+                            s_recs + (size_t)(valid ? h : 0) * RecPipe::stride);
       }
       mbar_arrive(&full[s]);
     } else {
+      if (*((volatile int*)&s_fail)) break;
       if (!mbar_wait_bounded(&full[s], ph)) {
         if (atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
         break;
       }
-      run_tasks<OP, FEA_FP32_INTEGRATE, true, true>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, lnodes,
-                                                    (int)threadIdx.x - kPipeProducers, kPipeConsumers);
+      run_tasks<OP, FEA_FP32_INTEGRATE, true, true, RecPipe>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, s_gi,
+                                                             (int)threadIdx.x - kPipeProducers, kPipeConsumers);
       mbar_arrive(&empty[s]);
     }
   }
@@ -480,6 +558,8 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
   P.mu = E / (2.0 * (1.0 + nu));
   P.src = op->source;
   for (int c = 0; c < 3; ++c) P.f[c] = op->body_force[c];
+  P.lamf = (float)P.lam;
+  P.muf = (float)P.mu;
   for (int k = 0; k < kNumRules; ++k) {
     const RefRule& rr = host_rule(k);
     for (int q = 0; q < 8; ++q)
@@ -497,18 +577,21 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
     P.k2 = op->k2;
     P.diffusion = op->kind == FEA_OP_DIFFUSION;
     P.hex = host_rule(kRuleHex8);
+    P.helem_ln = RP.helem_ln;
   }
   if (geo) {
-    const uint32_t stage_bytes = (P.L.bar + 127u) & ~127u;
-    const size_t pipe_smem = 2 * (size_t)stage_bytes + 32;
-    if (pipe_smem <= kRowsMaxSmem) {
+    RowsArgs Q = P;
+    Q.L = rows_layout(RP, true, RecPipe::stride);
+    const uint32_t stage_bytes = (Q.L.bar + 127u) & ~127u;
+    const size_t pipe_smem = 2 * (size_t)stage_bytes + 32 + 24 * (size_t)RP.max_local;
+    if (pipe_smem <= kRowsMaxSmem && RP.helem_ln != nullptr) {
       int dev = 0, sms = 0;
       FEA_CUDA(cudaGetDevice(&dev));
       FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       const unsigned grid = (unsigned)std::min<int64_t>(RP.n_blocks, sms);
       auto kern = op->kind == FEA_OP_DIFFUSION ? k_block_pipe<FEA_OP_DIFFUSION> : k_block_pipe<FEA_OP_ELASTICITY>;
       FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem));
-      kern<<<grid, kPipeProducers + kPipeConsumers, pipe_smem, s>>>(P, stage_bytes);
+      kern<<<grid, kPipeProducers + kPipeConsumers, pipe_smem, s>>>(Q, stage_bytes);
       FEA_CUDA(cudaGetLastError());
       return FEA_OK;
     }

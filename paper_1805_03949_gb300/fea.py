@@ -145,11 +145,21 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dptr(t) -> ctypes.c_void_p:
+def _dptr(t, dtype=None, min_numel=None, name="tensor") -> ctypes.c_void_p:
+    """Device pointer of a contiguous CUDA tensor on the current device (None passes NULL).
+
+    dtype and min_numel, where given, are checked too: the library reads the
+    pointer as that element type and writes up to min_numel elements."""
     if t is None:
         return ctypes.c_void_p(None)
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
-        raise TypeError("expected a contiguous CUDA tensor")
+        raise TypeError(f"{name}: expected a contiguous CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name}: needs at least {min_numel} elements, has {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -220,13 +230,17 @@ def fea_pattern_size(h, ndof: int, stream=None) -> int:
 
 def fea_build_csr_pattern(h, ndof: int, row_ptr, col_idx, node_map, stream=None):
     """Write row_ptr (int64), col_idx (int32, or None) and node_map (int32, or None) CUDA tensors."""
-    _check(_lib.fea_build_csr_pattern(h, ndof, _dptr(row_ptr), _dptr(col_idx), _dptr(node_map), _stream(stream)))
+    n, _, mlen = fea_mesh_info(h)
+    _check(_lib.fea_build_csr_pattern(h, ndof, _dptr(row_ptr, torch.int64, n * ndof + 1, "row_ptr"),
+                                      _dptr(col_idx, torch.int32, name="col_idx"),
+                                      _dptr(node_map, torch.int32, mlen, "node_map"), _stream(stream)))
 
 
 def fea_assemble(op: "fea_operator", h, row_ptr, node_map, A, b, stream=None):
     """Overwrite A (float64 [nnz]) and b (float64 [n_nodes * ndof]) with the assembled system."""
-    _check(_lib.fea_assemble(ctypes.byref(op), h, _dptr(row_ptr), _dptr(node_map), _dptr(A), _dptr(b),
-                             _stream(stream)))
+    _check(_lib.fea_assemble(ctypes.byref(op), h, _dptr(row_ptr, torch.int64, name="row_ptr"),
+                             _dptr(node_map, torch.int32, name="node_map"), _dptr(A, torch.float64, name="A"),
+                             _dptr(b, torch.float64, name="b"), _stream(stream)))
 
 
 def fea_check(h, stream=None):
@@ -240,7 +254,9 @@ def fea_row_ptr_from_counts_noalloc(counts, row_ptr, stream=None):
     For callers that cannot let the library allocate device memory; see the
     declaration in fea_gb300.h for the size limit and the shared scratch.
     """
-    _check(_lib.fea_row_ptr_from_counts_noalloc(_dptr(counts), int(counts.numel()), _dptr(row_ptr),
+    n = int(counts.numel())
+    _check(_lib.fea_row_ptr_from_counts_noalloc(_dptr(counts, torch.int32, name="counts"), n,
+                                                _dptr(row_ptr, torch.int64, n + 1, name="row_ptr"),
                                                 _stream(stream)))
 
 

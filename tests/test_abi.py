@@ -9,6 +9,7 @@ import re
 import pytest
 
 from paper_1805_03949_gb300 import build
+from tests.helpers import engine
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -135,3 +136,20 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(value) == expect, (cname, field, value, expect)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+@pytest.mark.gpu
+def test_binding_checks_pointer_types_and_sizes():
+    """The binding refuses a tensor whose dtype or length the C side would misread or overrun."""
+    fea = engine()
+    import torch
+    counts = torch.ones(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        fea.fea_row_ptr_from_counts_noalloc(counts, torch.zeros(10, dtype=torch.int64, device="cuda"))
+    with pytest.raises(TypeError):
+        fea.fea_row_ptr_from_counts_noalloc(counts.to(torch.int64), torch.zeros(11, dtype=torch.int64,
+                                                                                device="cuda"))
+    with pytest.raises(TypeError):
+        fea.fea_row_ptr_from_counts_noalloc(counts, torch.zeros(11, dtype=torch.int32, device="cuda"))
+    with pytest.raises(TypeError):
+        fea.fea_row_ptr_from_counts_noalloc(counts.cpu(), torch.zeros(11, dtype=torch.int64))

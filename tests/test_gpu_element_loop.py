@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_1805_03949_gb300 import meshgen as mg
-from tests.helpers import engine
+from tests.helpers import FP64_TOL, engine, j2_point_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -54,10 +54,15 @@ def test_element_loop_matches_oracle(oracle, name, schedule):
         fea.fea_check(h)
         mask = np.arange(8)[None, :] < np.array([4, 8, 6, 8])[mesh.types][:, None]
         s_st, s_sig = st.cpu().numpy(), sig.cpu().numpy()
-        assert np.abs(s_st[mask] - r2["state"][mask]).max() <= 1e-10 * np.abs(r2["state"]).max()
-        assert np.abs(s_sig[mask] - r2["stress"][mask]).max() <= 1e-10 * np.abs(r2["stress"]).max()
-        assert (yl.cpu().numpy()[mask] == r2["yielded"][mask]).mean() >= 0.999
-        assert (it.cpu().numpy()[mask] == r2["iters"][mask]).mean() >= 0.99
+        # every point, at the FP64 bar of its own normwise scale (no exemption:
+        # a tie in the yield or stopping test moves the state far less)
+        err_st, err_sig = j2_point_errors(s_st, s_sig, r2["state"], r2["stress"], mask)
+        y_mis = int((yl.cpu().numpy()[mask] != r2["yielded"][mask]).sum())
+        it_mis = int((it.cpu().numpy()[mask] != r2["iters"][mask]).sum())
+        print(f"{name} {schedule}: {int(mask.sum())} points, state err {err_st:.2e}, stress err {err_sig:.2e}, "
+              f"yield mismatches {y_mis}, iteration mismatches {it_mis}")
+        assert err_st <= FP64_TOL and err_sig <= FP64_TOL, (err_st, err_sig)
+        assert y_mis <= 0.001 * mask.sum() and it_mis <= 0.01 * mask.sum(), (y_mis, it_mis)
         assert r2["yielded"][mask].any() and not r2["yielded"][mask].all()
     finally:
         fea.fea_mesh_destroy(h)

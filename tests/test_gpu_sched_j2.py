@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1805_03949_gb300 import meshgen as mg
-from tests.helpers import FP32_TOL, FP64_TOL, engine, err_vs_oracle
+from tests.helpers import FP32_TOL, FP64_TOL, engine, err_vs_oracle, j2_point_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -125,8 +125,10 @@ def test_j2_two_steps_match_oracle(oracle, name, precision, variant):
     if name not in _J2REF:
         r1 = oracle.j2_assemble(mesh, 0.5 * U)
         r2 = oracle.j2_assemble(mesh, U, r1["state"])
-        _J2REF[name] = (r1, r2)
-    r1, r2 = _J2REF[name]
+        p1 = oracle.j2_points(mesh, 0.5 * U)
+        p2 = oracle.j2_points(mesh, U, r1["state"])   # the same update, with the stresses (per-point scales)
+        _J2REF[name] = (r1, r2, p1, p2)
+    r1, r2, p1, p2 = _J2REF[name]
     scatter = 1 if variant == "color" else 0
     schedule = 1 if variant == "steal" else 0
     s = fea.System.from_mesh(mesh, 3)
@@ -141,13 +143,17 @@ def test_j2_two_steps_match_oracle(oracle, name, precision, variant):
     assert errA <= tol and errb <= tol and zA <= tol and zb <= tol, (errA, errb, zA, zb)
     mask = np.arange(8)[None, :] < _nq(mesh.types)[:, None]
     assert r2["yielded"][mask].any() and not r2["yielded"][mask].all()   # a mixed elastic / plastic state
-    # yield decisions and the state are FP64 on both sides: identical up to rounding-order ties
-    assert (y1[mask] == r1["yielded"][mask]).mean() >= 0.999
-    assert (y2[mask] == r2["yielded"][mask]).mean() >= 0.999
-    s2 = st2.cpu().numpy()
-    scale = np.abs(r2["state"]).max()
-    assert np.abs(s2[mask] - r2["state"][mask]).max() <= 1e-10 * scale
-    assert (it2[mask] == r2["iters"][mask]).mean() >= 0.99
+    # the return map is FP64 in both precisions: every point's state (after
+    # each step) at the FP64 bar of its own normwise scale, with no exemption
+    assert np.array_equal(p1["state"], r1["state"]) and np.array_equal(p2["state"], r2["state"])
+    err1, _ = j2_point_errors(st1.cpu().numpy(), None, r1["state"], p1["stress"], mask)
+    err2, _ = j2_point_errors(st2.cpu().numpy(), None, r2["state"], p2["stress"], mask)
+    y_mis = int((y1[mask] != r1["yielded"][mask]).sum()) + int((y2[mask] != r2["yielded"][mask]).sum())
+    it_mis = int((it2[mask] != r2["iters"][mask]).sum())
+    print(f"{name} precision {precision} {variant}: {int(mask.sum())} points, state err {err1:.2e} / {err2:.2e}, "
+          f"yield mismatches {y_mis}, iteration mismatches {it_mis}")
+    assert err1 <= FP64_TOL and err2 <= FP64_TOL, (err1, err2)
+    assert y_mis <= 0.002 * mask.sum() and it_mis <= 0.01 * mask.sum(), (y_mis, it_mis)
     assert it2[mask].max() <= 12
 
 
