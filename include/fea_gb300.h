@@ -231,6 +231,16 @@ typedef struct {
                                 (m = rho0 / (beta dt^2); 0: a static Newton step) */
 } fea_operator;
 
+/* Launch parameters of an assembly on one mesh, as fea_autotune chose them. */
+typedef struct fea_tuning {
+  int32_t block_elems;      /* elements per block of FEA_SCATTER_BLOCK */
+  int32_t producer_warps;   /* geometry-producer warps (of 16) of the pipelined block-task kernel */
+  int32_t rows_block_nodes; /* nodes per block of FEA_SCATTER_ROWS */
+  int32_t chunk;            /* elements per work item (FEA_SCHED_STEAL) or per subdomain (MULTIDEP) */
+  float ms;                 /* median time of one assembly with these parameters */
+  int32_t candidates;       /* configurations timed */
+} fea_tuning;
+
 typedef struct fea_mesh fea_mesh;
 
 /* Message of the last failing call on this thread ("" if none).  A service
@@ -491,6 +501,32 @@ int fea_mesh_set_rows_block(fea_mesh* mesh, int block_nodes);
  * Host call. */
 int fea_mesh_set_block_elems(fea_mesh* mesh, int block_elems);
 
+/* Producer warps (4..8 of the 16) of the pipelined block-task kernel, which
+ * FEA_SCATTER_BLOCK uses for hex meshes in FEA_FP32_INTEGRATE: they compute
+ * the next block's geometry while the others run the current block's tasks
+ * (the local partitioning of Sec. 3.2.1 with its element work split in two
+ * stages).  Default 6.  Host call. */
+int fea_mesh_set_pipe_split(fea_mesh* mesh, int producer_warps);
+
+/* Autotuner of the assembly's launch parameters on this mesh.  The paper
+ * tunes the chunk size of its task-based assembly by hand (Sec. 5.2, the
+ * study of elements per task); here every candidate of the parameters that
+ * op's path uses is timed -- the median of `reps` assemblies with CUDA events
+ * on `stream`, after one untimed call that builds any plan -- and the fastest
+ * is kept:
+ *   FEA_SCATTER_MULTIDEP        subdomain size (op->chunk) 64, 128, 256
+ *   FEA_SCHED_STEAL             work-item size (op->chunk) 16 .. 256
+ *   FEA_SCATTER_ROWS            nodes per block 32, 64, 96, 128
+ *   FEA_SCATTER_BLOCK           elements per block 32, 48, 64, 80 (x producer
+ *                               warps 4 .. 8 where the pipelined kernel runs)
+ * (other paths: the current configuration is timed).  The mesh's setters and
+ * op->chunk are left at the choice, and A and b hold an assembly with it.
+ * The values are assembled by the same arithmetic under every candidate; only
+ * the FP64 summation order of an entry's contributions may change.
+ * Synchronous; host work for plan rebuilds. */
+int fea_autotune(fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d, const int32_t* node_map_d, double* A_d,
+                 double* b_d, int reps, void* stream, fea_tuning* out);
+
 /* Statistics of the current FEA_SCATTER_ROWS plan (Sec. 3.1; zeros if none):
  * info[0] blocks, [1] nodes per block, [2] max local nodes of a block,
  * [3] max halo elements of a block, [4] entry tasks, [5] element
@@ -538,6 +574,16 @@ int fea_assemble_launches(const fea_operator* op, const fea_mesh* mesh, int* n_k
  * it).  Service.  FEA_ERR_INVERTED_ELEMENT names the first element id found in the
  * message.  Synchronous. */
 int fea_check(fea_mesh* mesh, void* stream);
+
+/* Measured arithmetic peak of the current device: the FP64 (kind 0) or FP32
+ * (kind 1) rate of fused multiply-adds, in flop/s (an FMA is 2 flop).  The
+ * paper has no counterpart: it is the microbenchmark behind the FP64 and FP32
+ * denominators of the assembly roofline (T_roof = max(FP64 flop / P64, FP32
+ * flop / P32, bytes / HBM bandwidth)).  Every SM runs 8 independent FMA
+ * chains per thread for `iters` (>= 4) steps, after a shorter warm-up launch;
+ * the rate is taken over the CUDA-event time of the timed launch on `stream`.
+ * Allocates a small scratch buffer.  Synchronous. */
+int fea_peak_probe(int kind, int64_t iters, double* flops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -108,6 +108,7 @@ struct fea_mesh {
   fea::RowsPlan* blocks = nullptr;              // FEA_SCATTER_BLOCK plan (blocks.cu)
   fea::MultidepPlan* mdep = nullptr;            // FEA_SCATTER_MULTIDEP plan (multidep.cu)
   int block_elems = 64;                         // elements per block of FEA_SCATTER_BLOCK
+  int pipe_producer_warps = 6;                  // producer warps of the pipelined block-task kernel (4..8 of 16)
   int rows_block_nodes = 64;
   // persistent schedules (persistent.cu): work items of the last chunk size
   int items_chunk = 0;

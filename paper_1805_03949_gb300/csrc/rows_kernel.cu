@@ -396,31 +396,35 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 // decision to stop after a timeout is taken there by all of them at once, so
 // none is left waiting.  Every wait is bounded; a timeout latches
 // FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
-// Measured splits per 128^3 step: 6 + 8 warps 5.79 ms, 6 + 10 5.48, 6 + 12
-// 5.95 (register cap), 4 + 12 6.14, 7 + 9 5.90.
+// The split between producer and consumer warps (PW + 16 - PW) is a
+// template parameter, chosen per mesh (fea_mesh_set_pipe_split, or the
+// autotuner).
 // ---------------------------------------------------------------------------
-constexpr int kPipeProducers = 192;
-constexpr int kPipeConsumers = 320;
+constexpr int kPipeThreads = 512;
 constexpr int kPipeProducerBar = 1;
 
-// all producer threads arrive; true when pred holds on any of them
+// all NP producer threads arrive; true when pred holds on any of them
+template <int NP>
 __device__ __forceinline__ bool producers_any(bool pred) {
   int r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((int)pred), "n"(kPipeProducerBar), "n"(kPipeProducers)
+      : "r"((int)pred), "n"(kPipeProducerBar), "n"(NP)
       : "memory");
   return r != 0;
 }
 
+template <int NP>
 __device__ __forceinline__ void producers_sync() {
-  asm volatile("bar.sync %0, %1;" ::"n"(kPipeProducerBar), "n"(kPipeProducers) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"n"(kPipeProducerBar), "n"(NP) : "memory");
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
+template <int OP, int PW>
+__global__ void __launch_bounds__(kPipeThreads, 1)
     k_block_pipe(const __grid_constant__ RowsArgs P, uint32_t stage_bytes) {
+  constexpr int kPipeProducers = 32 * PW;
+  constexpr int kPipeConsumers = kPipeThreads - kPipeProducers;
   extern __shared__ __align__(128) unsigned char pipe_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(pipe_raw + 2 * stage_bytes);
   uint64_t* empty = full + 2;
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
       if (!ok && atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
       // one decision for every producer; past this barrier, every producer has
       // also finished reading the coordinate copy of the previous block
-      if (producers_any(*((volatile int*)&s_fail) != 0)) break;
+      if (producers_any<kPipeProducers>(*((volatile int*)&s_fail) != 0)) break;
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
         mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
@@ -479,7 +483,7 @@ __global__ void __launch_bounds__(kPipeProducers + kPipeConsumers, 1)
 #pragma unroll
         for (int c = 0; c < 3; ++c) s_x[3 * t + c] = P.coords[3 * (int64_t)node + c];
       }
-      producers_sync();
+      producers_sync<kPipeProducers>();
       for (int h0 = 0; h0 < H.n_helem; h0 += kPipeProducers / 8) {
         // a warp holds 4 elements; one with none left skips the pass (its
         // modal transform would run on the FP64 pipe for nothing)
@@ -589,9 +593,17 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
       FEA_CUDA(cudaGetDevice(&dev));
       FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       const unsigned grid = (unsigned)std::min<int64_t>(RP.n_blocks, sms);
-      auto kern = op->kind == FEA_OP_DIFFUSION ? k_block_pipe<FEA_OP_DIFFUSION> : k_block_pipe<FEA_OP_ELASTICITY>;
+      const bool dif = op->kind == FEA_OP_DIFFUSION;
+      void (*kern)(const RowsArgs, uint32_t) = nullptr;
+      switch (m->pipe_producer_warps) {
+        case 4: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 4> : k_block_pipe<FEA_OP_ELASTICITY, 4>; break;
+        case 5: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 5> : k_block_pipe<FEA_OP_ELASTICITY, 5>; break;
+        case 7: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 7> : k_block_pipe<FEA_OP_ELASTICITY, 7>; break;
+        case 8: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 8> : k_block_pipe<FEA_OP_ELASTICITY, 8>; break;
+        default: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 6> : k_block_pipe<FEA_OP_ELASTICITY, 6>; break;
+      }
       FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem));
-      kern<<<grid, kPipeProducers + kPipeConsumers, pipe_smem, s>>>(Q, stage_bytes);
+      kern<<<grid, kPipeThreads, pipe_smem, s>>>(Q, stage_bytes);
       FEA_CUDA(cudaGetLastError());
       return FEA_OK;
     }

@@ -48,6 +48,12 @@ class fea_mesh_desc(ctypes.Structure):
                 ("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class fea_tuning(ctypes.Structure):
+    _fields_ = [("block_elems", ctypes.c_int32), ("producer_warps", ctypes.c_int32),
+                ("rows_block_nodes", ctypes.c_int32), ("chunk", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
+
+
 class fea_batch_entry(ctypes.Structure):
     _fields_ = [("mesh", ctypes.c_void_p), ("row_ptr_d", ctypes.c_void_p), ("node_map_d", ctypes.c_void_p),
                 ("A_d", ctypes.c_void_p), ("b_d", ctypes.c_void_p)]
@@ -118,6 +124,9 @@ def _load():
         "fea_mesh_set_block_elems": (I32, [P, I32]),
         "fea_multidep_plan": (I32, [P, I32, ctypes.POINTER(I64), P, P, P, P]),
         "fea_multidep_hold": (I32, [P, I32, I32]),
+        "fea_peak_probe": (I32, [I32, I64, ctypes.POINTER(ctypes.c_double), P]),
+        "fea_mesh_set_pipe_split": (I32, [P, I32]),
+        "fea_autotune": (I32, [ctypes.POINTER(fea_operator), P, P, P, P, P, I32, P, ctypes.POINTER(fea_tuning)]),
     }
     for name, (rt, at) in sig.items():
         f = getattr(lib, name)
@@ -268,6 +277,46 @@ def fea_mesh_set_rows_block(h, block_nodes: int):
 def fea_mesh_set_block_elems(h, block_elems: int):
     """Elements per block of the block-task scatter."""
     _check(_lib.fea_mesh_set_block_elems(h, int(block_elems)))
+
+
+def fea_mesh_set_pipe_split(h, producer_warps: int):
+    """Producer warps (4..8 of 16) of the pipelined block-task kernel."""
+    _check(_lib.fea_mesh_set_pipe_split(h, int(producer_warps)))
+
+
+def fea_autotune(op: "fea_operator", h, row_ptr, node_map, A, b, reps: int = 5, stream=None) -> dict:
+    """Time the candidate launch parameters of op's path on the mesh, keep the fastest (see the header)."""
+    t = fea_tuning()
+    _check(_lib.fea_autotune(ctypes.byref(op), h, _dptr(row_ptr, torch.int64, name="row_ptr"),
+                             _dptr(node_map, torch.int32, name="node_map"), _dptr(A, torch.float64, name="A"),
+                             _dptr(b, torch.float64, name="b"), int(reps), _stream(stream), ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in fea_tuning._fields_}
+
+
+def autotune(op: "fea_operator", system: "System", key: str, cache: str | None = None, reps: int = 5) -> dict:
+    """fea_autotune with a JSON cache: the choice for `key` (a name for the mesh
+    and operator) is read from `cache` if present and applied without timing;
+    otherwise it is timed and written there."""
+    import json
+    entries = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            entries = json.load(f)
+    if key in entries:
+        c = entries[key]
+        fea_mesh_set_block_elems(system.handle, c["block_elems"])
+        fea_mesh_set_pipe_split(system.handle, c["producer_warps"])
+        fea_mesh_set_rows_block(system.handle, c["rows_block_nodes"])
+        op.chunk = c["chunk"]
+        return dict(c, cached=True)
+    c = fea_autotune(op, system.handle, system.row_ptr, system.node_map, system.A, system.b, reps)
+    if cache:
+        entries[key] = c
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return dict(c, cached=False)
 
 
 def fea_rows_plan_info(h) -> dict:
@@ -471,6 +520,13 @@ def fea_element_loop_grid(op: "fea_operator", h) -> int:
     n = ctypes.c_int32()
     _check(_lib.fea_element_loop_grid(ctypes.byref(op), h, ctypes.byref(n)))
     return int(n.value)
+
+
+def fea_peak_probe(kind: int, iters: int, stream=None) -> float:
+    """Measured FMA rate of the current GPU in flop/s: kind 0 FP64, 1 FP32."""
+    f = ctypes.c_double()
+    _check(_lib.fea_peak_probe(int(kind), int(iters), ctypes.byref(f), _stream(stream)))
+    return f.value
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:

@@ -100,6 +100,9 @@ def test_every_entry_point_rejects_a_null_handle(clib):
         "fea_color_info": (None, None, ctypes.byref(k)),
         "fea_assemble_launches": (None, None, ctypes.byref(k)),
         "fea_pack_lpt": (None, I64(1), 1, None, None, None),
+        "fea_peak_probe": (0, I64(1000), None, None),
+        "fea_mesh_set_pipe_split": (None, 6),
+        "fea_autotune": (None, None, None, None, None, None, 3, None, None),
     }
     for name, args in calls.items():
         assert getattr(clib, name)(*args) == -1, name
@@ -115,7 +118,7 @@ def test_binding_structs_match_the_header(tmp_path):
     probe = tmp_path / "layout.c"
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fea_gb300.h"', 'int main(void) {']
     structs = {"fea_operator": fea.fea_operator, "fea_mesh_desc": fea.fea_mesh_desc,
-               "fea_batch_entry": fea.fea_batch_entry}
+               "fea_batch_entry": fea.fea_batch_entry, "fea_tuning": fea.fea_tuning}
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
         for field, _ in cls._fields_:
@@ -153,3 +156,21 @@ def test_binding_checks_pointer_types_and_sizes():
         fea.fea_row_ptr_from_counts_noalloc(counts, torch.zeros(11, dtype=torch.int32, device="cuda"))
     with pytest.raises(TypeError):
         fea.fea_row_ptr_from_counts_noalloc(counts.cpu(), torch.zeros(11, dtype=torch.int64))
+
+
+def test_peak_probe_rejects_bad_arguments(clib):
+    f = ctypes.c_double()
+    assert clib.fea_peak_probe(2, ctypes.c_int64(1000), ctypes.byref(f), None) == -1
+    assert clib.fea_peak_probe(0, ctypes.c_int64(3), ctypes.byref(f), None) == -1
+
+
+@pytest.mark.gpu
+def test_peak_probe_measures_the_fma_rates():
+    """FP64 near GB300's nominal 1.25 TFLOP/s (2 FP64 FMA per SM and clock),
+    FP32 near 152 SMs x 128 lanes x 2 flop x clock; FP32 far above FP64."""
+    fea = engine()
+    p64 = fea.fea_peak_probe(0, 20000)
+    p32 = fea.fea_peak_probe(1, 200000)
+    assert 0.6e12 < p64 < 1.5e12, p64
+    assert 40e12 < p32 < 90e12, p32
+    assert p32 > 30 * p64
