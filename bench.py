@@ -63,6 +63,22 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def measured_peaks(fea):
+    """Roofline denominators: HBM copy bandwidth (MEASURED_PEAKS.json) and the FP64 and
+    FP32 FMA rates measured on this GPU by the engine's probe (nominal where it fails)."""
+    hbm, kind = _peaks()
+    out = {"hbm": hbm * 1e9, "hbm_source": kind,
+           "fp64_nominal": NOMINAL_FP64_TFLOPS * 1e12, "fp32_nominal": NOMINAL_FP32_TFLOPS * 1e12}
+    for key, k, iters in (("fp64", 0, 20000), ("fp32", 1, 1000000)):
+        try:
+            out[key] = fea.fea_peak_probe(k, iters)
+            out[key + "_source"] = "measured (fea_peak_probe: FMA chains on every SM, CUDA events)"
+        except Exception as e:  # noqa: BLE001 -- report the nominal rate instead
+            out[key] = out[key + "_nominal"]
+            out[key + "_source"] = f"nominal (probe failed: {e})"
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -133,6 +149,10 @@ VARIANTS = {
     "fp32a_atomic": (2, "ATOMIC"),
     "fp32a_rows": (2, "ROWS"),
 }
+
+
+# variants whose launch parameters the autotuner picks before they are timed
+TUNED_VARIANTS = ("fp32_block", "fp32_rows", "fp32_multidep")
 
 
 def variant_operators(fea) -> dict:
@@ -213,13 +233,17 @@ def element_flops(etype, op, nq, k_varies=False):
     coords (FP64, diffusion with k = k0 + k2 x^2 only): x_q = sum_a N_a x_a,
       nn FMA per point.
     grad: the scaled gradients g_a = s C grad_xi N_a, 9 FMA + 3 mul per node
-      and 3 for s, per point (once for an affine tet, whose gradients are
-      constant).
-    prod: diffusion, per (a <= b) pair a dot product (3 FMA) and its weight
-      (1 mul), and k_q (mul + FMA) per point; elasticity, per (a <= b) block 3
-      FMA (dot) + 18 FMA (lam g_a g_b^T + mu g_b g_a^T) + 3 adds (the diagonal),
-      and 6 mul per node (lam g_a, mu g_a).  Per point, except for affine tets,
-      whose products are taken once with the weight sum (1 FMA per point).
+      and 3 for s = sqrt(w det J) / det J, per point; an affine tet's gradients
+      are constant, taken once with s = 1 / det J from its geometry.
+    prod: diffusion, per point k_q g_a (3 mul per node) and, per (a <= b)
+      pair, 3 FMA accumulating k_q g_a . g_b into A_ab, plus k_q = k0 + k2 x_q^2
+      (mul + FMA) where k varies; elasticity, per point and (a <= b) block 3 FMA
+      (mu g_a . g_b) + 18 FMA (lam g_a g_b^T + mu g_b g_a^T into A_ab) + 3 adds
+      (the diagonal), and 6 mul per node (lam g_a, mu g_a).  An affine tet, whose
+      gradients are constant, takes its products once: the weight sum W =
+      sum_q w_q det J k_q (1 FMA per point, and k_q), then per pair a dot
+      product (3 FMA) times W (1 mul) for diffusion, per element lam W and mu
+      W (2 mul) and the elasticity block as above.
     rhs: w det J f_c N_a, 1 FMA per node, component and point.
     """
     nn = NODES_PER_TYPE[etype]
@@ -233,13 +257,13 @@ def element_flops(etype, op, nq, k_varies=False):
     else:
         geometry = 3 * (nn - 1) + nq * (2 * 9 * (nn - 1) + 27 + 5 + 1)
     coords = nq * 2 * nn if (op == OP_DIFFUSION and k_varies) else 0
-    grad = (1 if affine else nq) * (21 * nn + 3)
+    grad = 21 * nn if affine else nq * (21 * nn + 3)
+    kq = 3 if k_varies else 0
     if op == OP_DIFFUSION:
-        per = 7 * pairs
-        prod = (per + nq * (2 + 3) if affine else nq * (per + 3)) if k_varies else (per + 2 * nq if affine else nq * per)
+        prod = 7 * pairs + nq * (2 + kq) if affine else nq * (kq + 3 * nn + 6 * pairs)
     else:
         per = 45 * pairs + 6 * nn
-        prod = per + 2 * nq if affine else nq * per
+        prod = per + 2 + nq * (2 + kq) if affine else nq * per
     rhs = nq * 2 * nn * d
     return {"geometry": geometry, "coords": coords, "grad": grad, "prod": prod, "rhs": rhs}
 
@@ -264,8 +288,9 @@ def assembly_work(type_counts, n_nodes, nnz_node, op, precision, nq_of=None, k_v
 
     type_counts: {element type: count}; nnz_node: node-level nonzeros of the
     pattern (the scalar count is d^2 times it); precision 0 = FP64 (every
-    flop on the FP64 pipe), else FP32-integrate (geometry, coordinates, the
-    J2 update and the accumulation in FP64, the rest in FP32); nq_of: points
+    flop on the FP64 pipe), 1 = FP32-integrate (geometry, coordinates, the
+    J2 update and the accumulation in FP64, the rest in FP32), 2 =
+    FP32-adaptive (as 1 with the geometry in FP32); nq_of: points
     of each type's rule (default: the degree-2 rules, tet 4, pyr 8, prism 6,
     hex 8); j2: dict(points, plastic_points, newton_iters) summed over the
     mesh for the J2 operator (hex8 only).
@@ -312,6 +337,11 @@ def assembly_work(type_counts, n_nodes, nnz_node, op, precision, nq_of=None, k_v
         f64 += parts["integrate"]
     else:
         f32 = parts["integrate"]
+    if precision == 2:
+        # FP32-adaptive: the geometry of undistorted elements is FP32 (the few
+        # distorted ones redone in FP64 are not counted)
+        f64 -= parts["geometry"]
+        f32 += parts["geometry"]
     nnz = d * d * nnz_node
     by = 8 * nnz + n_nodes * (24 + 8 * d + 8 * d) + 4 * sum_nn + 4 * sum_nn2
     if op == OP_J2:
@@ -389,6 +419,12 @@ def run_ours(args, rank, world, local_rank):
     E, N = sysm.n_elems, sysm.n_nodes
 
     variants = variant_operators(fea)
+    # results sampled for the error report: every dof row of ~30 seeded nodes,
+    # copied to the host after each variant's timed region
+    check = rank == 0 and not args.no_oracle
+    rp_h = sysm.row_ptr.cpu().numpy() if check else None
+    nodes = sample_hex_nodes(args.n, 11) if check else None
+    snaps = {}
     if args.block_nodes:
         fea.fea_mesh_set_rows_block(sysm.handle, args.block_nodes)
     if args.only:
@@ -398,12 +434,18 @@ def run_ours(args, rank, world, local_rank):
     results = {}
     clocks = ClockSampler(local_rank, args.clocks_dir)
     clocks_started = False
+    tuned = {}
     for name, op in variants.items():
         fea.set_events(op, None)
         t_first = time.perf_counter()
         sysm.assemble(op)                            # first call builds any plan the variant needs
         sysm.check()
         plan_s[name] = time.perf_counter() - t_first
+        if name in TUNED_VARIANTS and not args.no_tune and not (name.endswith("rows") and args.block_nodes):
+            # block sizes, the producer/consumer split, subdomain size: timed by the engine's autotuner
+            t0 = time.perf_counter()
+            tuned[name] = fea.fea_autotune(op, sysm.handle, sysm.row_ptr, sysm.node_map, sysm.A, sysm.b, 5)
+            tuned[name]["seconds"] = time.perf_counter() - t0
         nk = fea.fea_assemble_launches(op, sysm.handle)
         steps = args.steps if name.startswith("fp32") else max(3, min(args.steps, 5))
         # one set of profiling events per timed step: events[0] before zeroing, [1] after,
@@ -447,6 +489,8 @@ def run_ours(args, rank, world, local_rank):
         total_ms = max_over_ranks(total_ms, dist, dev)
         results[name] = dict(ms_per_step=total_ms / steps, kernel_ms=kern_ms, zero_ms=zero_ms, main_ms=main_ms,
                              geo_ms=geo_ms, launches=nk, steps=steps)
+        if check:
+            snaps[name] = snapshot_rows(sysm, nodes, rp_h)
     clk = clocks.stop()
     # the assembled operator applied to a vector (partial-row product, Sec. 3.1),
     # on the system the last variant assembled
@@ -455,6 +499,22 @@ def run_ours(args, rank, world, local_rank):
         x = torch.randn(sysm.b.numel(), dtype=torch.float64, device=dev)
         y = torch.empty_like(x)
         sp_ms = _time_calls(lambda: fea.fea_spmv(sysm.handle, 3, sysm.row_ptr, sysm.A, x, y), 20)
+        sp_err = None
+        if check:
+            # the product's own rounding: sampled rows against the host FP64
+            # product of the same A (normwise: over sum_j |a_ij x_j|)
+            import torch as _t
+            xh = x.cpu().numpy()
+            rows = np.concatenate([3 * nodes + c for c in range(3)])
+            worst = 0.0
+            for r in rows:
+                lo, hi = int(rp_h[r]), int(rp_h[r + 1])
+                a = sysm.A[lo:hi].cpu().numpy()
+                cols = sysm.col_idx[lo:hi].cpu().numpy()
+                ax = a * xh[cols]
+                worst = max(worst, abs(float(y[r].item()) - float(ax.sum())) / float(np.abs(ax).sum()))
+            sp_err = {"y_normwise": worst, "rows": int(len(rows)),
+                      "reference": "host FP64 product of the same A, sampled rows"}
         sp_bytes = algorithmic_bytes_spmv(N, nnz)
         hbm_pk, _ = _peaks()
         # one FP64 FMA per stored value: on GB300 the FP64 pipe bounds the product
@@ -464,7 +524,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak_gbs": hbm_pk, "frac": sp_bytes / (sp_ms * 1e-3) / 1e9 / hbm_pk,
                 "fp64_gflops": 2 * nnz / (sp_ms * 1e-3) / 1e9, "fp64_frac": 2 * nnz / (sp_ms * 1e-3) / p64,
                 "floor_ms": {"hbm": sp_bytes / (hbm_pk * 1e9) * 1e3, "fp64": 2 * nnz / p64 * 1e3},
-                "bytes": "A 8 nnz, node columns 4 nnz/9, node row starts, row_ptr (one per node), x and y once"}
+                "bytes": "A 8 nnz, node columns 4 nnz/9, node row starts, row_ptr (one per node), x and y once",
+                "error": sp_err}
     # the finite-strain solid (Sec. 2.2, neo-Hookean reading) on the same mesh:
     # the Newton Jacobian and internal force at a smooth deformation
     neo = None
@@ -473,11 +534,15 @@ def run_ours(args, rank, world, local_rank):
         U = mg.fourier_displacement(mesh.coords, 0.004, seed=6) + 0.05 * mesh.coords[:, [1, 2, 0]]
         u_d = torch.tensor(U.reshape(-1), device=dev)
         neo = {"deformation": "fourier_displacement(0.004, seed 6) + 0.05 (y, z, x): strains of several %"}
+        nh_nodes = sample_hex_nodes(args.n, 13, count=12)
         for name, prec, steps in (("fp32_atomic", 1, 10), ("fp64_atomic", 0, 3)):
             op = fea.make_operator(kind=fea.FEA_OP_NEOHOOKE, precision=prec, u=u_d, young=1.0, poisson=0.3)
             ms = _time_calls(lambda: sysm.assemble(op), steps)
             sysm.check()
             neo[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3)}
+            if check:
+                neo[name]["_snap"] = snapshot_rows(sysm, nh_nodes, rp_h)
+        neo["_U"] = U
     fp32 = [k for k in results if k.startswith("fp32_")]
     head = args.variant if args.variant in results else min(fp32, key=lambda k: results[k]["ms_per_step"])
 
@@ -532,26 +597,23 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         r = results[head]
-        hbm, peak_kind = _peaks()
+        pk = measured_peaks(fea)
+        hbm, peak_kind = pk["hbm"] / 1e9, pk["hbm_source"]
         by = algorithmic_bytes(N, E, nnz)
         fl = algorithmic_flops_hex_elasticity(E, N, nnz)
-        p64 = NOMINAL_FP64_TFLOPS * 1e12
-        p32 = NOMINAL_FP32_TFLOPS * 1e12
-        # whole step: T_roof = max(FP64 flops / FP64 peak, FP32 flops / FP32 peak, bytes / HBM)
-        comp = {"fp64_ms": fl["fp64"] / p64 * 1e3 if "fp32" in head else None,
-                "fp32_ms": fl["fp32"] / p32 * 1e3, "hbm_ms": by / (hbm * 1e9) * 1e3}
-        t_roof = max(v for v in comp.values() if v is not None)
-        step_roof = dict(comp, t_roof_ms=t_roof, bound=max((k for k in comp if comp[k] is not None),
-                                                            key=lambda k: comp[k])[:-3],
-                         frac=t_roof / r["ms_per_step"])
+        p64 = pk["fp64"]
+        # whole step of every variant: T_roof = max(FP64 flops / P64, FP32 flops / P32, bytes / HBM)
+        step_roofs = {k: step_roofline(assembly_work({3: E}, N, nnz // 9, OP_ELASTICITY, VARIANTS[k][0]),
+                                       v["ms_per_step"], pk) for k, v in results.items()}
+        step_roof = step_roofs[head]
         # dominant kernel of the step, against the roofline that bounds it
         kind = head.split("_", 1)[1]
         fused = kind == "block" and r["launches"] == 1   # the geometry runs inside the task kernel
+        p64_note = {"peak_source": pk["fp64_source"], "peak_nominal": NOMINAL_FP64_TFLOPS * 1e3}
         if kind in ("rows", "block") and not fused and r["geo_ms"] > r["main_ms"]:
             k_name, k_ms = "k_geometry", r["geo_ms"]
-            roof = {"bound": "alu", "achieved": fl["fp64_geometry"] / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
-                    "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (NVIDIA, dense)",
-                    "work": "FP64 geometry"}
+            roof = dict({"bound": "alu", "achieved": fl["fp64_geometry"] / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
+                         "unit": "GFLOP/s (FP64)", "work": "FP64 geometry"}, **p64_note)
         elif kind in ("rows", "block") and not fused:
             k_name, k_ms = DOMINANT_KERNEL[kind], r["main_ms"]
             plan = fea.fea_rows_plan_info(sysm.handle) if kind == "rows" else {"bytes": 0}
@@ -565,14 +627,16 @@ def run_ours(args, rank, world, local_rank):
             on_sm = kind != "atomic"
             f64 = fl["fp64"] if on_sm else fl["fp64_geometry"]
             if "fp32_" in head and f64 / p64 > by / (hbm * 1e9):
-                roof = {"bound": "alu", "achieved": f64 / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
-                        "unit": "GFLOP/s (FP64)", "peak_source": "nominal FP64 of the GB300 (NVIDIA, dense)",
-                        "work": "FP64 geometry + the minimal FP64 accumulation adds" if on_sm else "FP64 geometry"}
+                roof = dict({"bound": "alu", "achieved": f64 / (k_ms * 1e-3) / 1e9, "peak": p64 / 1e9,
+                             "unit": "GFLOP/s (FP64)", "work": "FP64 geometry + the minimal FP64 accumulation adds"
+                             if on_sm else "FP64 geometry"}, **p64_note)
             else:
                 roof = {"bound": "hbm", "achieved": by / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                         "peak_source": peak_kind, "algorithmic_bytes": by}
         roof.update(frac=roof["achieved"] / roof["peak"], kernel=k_name, kernel_ms=k_ms,
                     traffic=TRAFFIC_BYTES.get(k_name.split()[0]) if args.n == 128 else None)
+        if "peak_nominal" in roof:
+            roof["frac_nominal"] = roof["achieved"] / roof["peak_nominal"]
         line = {
             "metric": METRIC,
             "value": whole_job_rate(E, world, r["ms_per_step"]),
@@ -591,6 +655,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world} (partial-row, no exchange)"},
             "roofline": roof,
             "step_roofline": step_roof,
+            "peaks": {k: v for k, v in pk.items()},
             "comparator": {"variant": "fp64_atomic",
                            "value": world * E / (results["fp64_atomic"]["ms_per_step"] * 1e-3),
                            "ms_per_step": results["fp64_atomic"]["ms_per_step"],
@@ -598,9 +663,11 @@ def run_ours(args, rank, world, local_rank):
             "variants": {k: {"ms_per_step": v["ms_per_step"], "zero_ms": v["zero_ms"], "kernels_ms": v["kernel_ms"],
                              "main_kernel_ms": v["main_ms"], "geometry_ms": v["geo_ms"],
                              "launches_per_step": v["launches"],
-                             "elements_per_s": E / (v["ms_per_step"] * 1e-3)} for k, v in results.items()},
+                             "elements_per_s": E / (v["ms_per_step"] * 1e-3),
+                             "step_roofline": step_roofs[k]} for k, v in results.items()},
             "pattern_build_s": pattern_s,
             "first_call_s": plan_s,
+            "autotuned": tuned,
             "rows_plan": fea.fea_rows_plan_info(sysm.handle),
             "spmv": spmv,
             "neohooke": neo,
@@ -611,12 +678,25 @@ def run_ours(args, rank, world, local_rank):
                     "host_numa_node": host_numa},
             "gpu_launches": r["launches"] * r["steps"],
         }
-        if not args.no_cpu_baseline:
+        nh_snaps = {k: neo[k].pop("_snap") for k in list(neo) if isinstance(neo[k], dict) and "_snap" in neo[k]}
+        nh_U = neo.pop("_U")
+        if not (args.no_cpu_baseline or args.no_oracle):
             line["cpu_baseline"] = cpu_baseline(args)
+        if check:
+            # oracle leg: the error of every variant's sampled rows (after every timed region)
+            ref = oracle_rows(mesh, nodes, OP_ELASTICITY, young=1.0, poisson=0.3)
+            errs = {k: row_errors(sn, ref, 1e-12 if VARIANTS[k][0] == 0 else 1e-5) for k, sn in snaps.items()}
+            sample = f"every dof row of {len(nodes)} seeded nodes (corners, edges, faces, interior), oracle rows"
+            line["error"] = dict(errs[head], sample=sample)
+            line["errors"] = errs
+            if nh_snaps:
+                nh_ref = oracle_nh_rows(mesh, nh_U, nh_nodes)
+                for k, sn in nh_snaps.items():
+                    neo[k]["error"] = row_errors(sn, nh_ref, 1e-12 if k.startswith("fp64") else 1e-5)
         if world == 1 and args.workloads:
             sysm.close()
             torch.cuda.empty_cache()
-            line["workloads"] = other_workloads(args, dev)
+            line["workloads"] = other_workloads(args, dev, pk)
         print(json.dumps(line), flush=True)
     sysm.close()
     if dist is not None:
@@ -668,18 +748,21 @@ def _time_calls(fn, steps, warmup=2):
     return float(statistics.median(ts))
 
 
-def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, grid_fn=None):
+def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, grid_fn=None, snap=None):
     """Persistent schedules of one workload: work stealing (whose per-item timings train the
     cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, and
-    the same queues with stealing as the fallback once a CTA's own queue is empty."""
+    the same queues with stealing as the fallback once a CTA's own queue is empty.  snap(name)
+    is called after each schedule's timed calls (results sampled for the error report)."""
     import torch
     from paper_1805_03949_gb300 import meshgen as mg
     run = run or s.assemble
     grid_fn = grid_fn or fea.fea_persistent_grid
+    snap = snap or (lambda name: None)
     item_ns = torch.zeros(len(counts), dtype=torch.int64, device=dev)
     steal = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, chunk=chunk, item_ns=item_ns, **base)
     out = {"persistent_steal": _time_calls(lambda: run(steal), steps)}
     s.check()
+    snap("persistent_steal")
     y = torch.log(item_ns.to(torch.float32) / torch.tensor(counts, device=dev, dtype=torch.float32))
     h = fea.fea_costmodel_create(6, mg.mlp_initial_params(6).astype(np.float32))
     t0 = time.perf_counter()
@@ -698,13 +781,54 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, 
             op = fea.make_operator(schedule=mode, n_ctas=grid, queue=qd, queue_off=od, chunk=chunk, **base)
             out[f"{name}_queues{suffix}"] = _time_calls(lambda: run(op), steps)
             s.check()
+            snap(f"{name}_queues{suffix}")
     return out, {"train_loss": loss, "train_s": train_s, "epochs": 600, "items": len(counts), "chunk": chunk,
                  "grid": grid,
                  "gain_static": out["gauss_points_queues"] / out["mlp_queues"] - 1.0,
                  "gain_with_steal": out["gauss_points_queues_steal"] / out["mlp_queues_steal"] - 1.0}
 
 
-def workload_hybrid(dev, steps=5):
+def _type_counts(mesh):
+    return {t: int(c) for t, c in enumerate(np.bincount(np.asarray(mesh.types), minlength=4)) if c}
+
+
+def _rooflines(ms, work_of, pk):
+    """Step roofline of every timed variant: work_of(variant) -> assembly_work(...)."""
+    return {k: step_roofline(work_of(k), v, pk) for k, v in ms.items()}
+
+
+def workload_poisson(dev, pk, check, steps=20):
+    """Scalar Poisson P1 on 16^3 Kuhn tets (24,576 elements, 1-point rule, FP64): a
+    correctness-sized problem that fits in L2, bounded by launch latency."""
+    from paper_1805_03949_gb300 import fea, meshgen as mg
+    mesh = mg.kuhn_tet_cube(16)
+    s = fea.System.from_mesh(mesh, 1, device=dev, with_cols=False)
+    try:
+        kw = dict(kind=0, tet_rule=0, k0=1.0, k2=0.0, source=1.0)
+        out, snaps = {}, {}
+        for name, op in (("fp64_per_type", fea.make_operator(precision=0, **kw)),
+                         ("fp32_per_type", fea.make_operator(precision=1, **kw)),
+                         ("fp64_steal", fea.make_operator(precision=0, schedule=fea.FEA_SCHED_STEAL, **kw))):
+            out[name] = _time_calls(lambda: s.assemble(op), steps)
+            s.check()
+            if check:
+                snaps[name] = (s.A.cpu().numpy(), s.b.cpu().numpy())
+        nnz_node = s.A.numel()
+        prec = {"fp64_per_type": 0, "fp32_per_type": 1, "fp64_steal": 0}
+        roof = _rooflines(out, lambda k: assembly_work(_type_counts(mesh), mesh.n_nodes, nnz_node, OP_DIFFUSION,
+                                                       prec[k], nq_of={0: 1}), pk)
+        res = {"workload": "Poisson P1, 16^3 Kuhn tets (24,576 elements, 4,913 nodes), 1-point rule, f = 1",
+               "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()},
+               "roofline": roof, "bound_note": "the whole problem (about 2 MB) lives in L2: launch latency bounds it"}
+        if check:
+            res["error"] = oracle_full_errors(mesh, snaps, prec, OP_DIFFUSION, tet_rule=0, k0=1.0, k2=0.0,
+                                              source=1.0)
+        return res
+    finally:
+        s.close()
+
+
+def workload_hybrid(dev, pk, check, steps=5):
     """Hybrid tet/pyramid/prism/hex diffusion, k = 1 + x^2, degree-2 rules: per-type launches
     against one persistent launch over every type, scheduled by stealing or by packed queues."""
     from paper_1805_03949_gb300 import fea, meshgen as mg
@@ -712,24 +836,45 @@ def workload_hybrid(dev, steps=5):
     s = fea.System.from_mesh(mesh, 1, device=dev, with_cols=False)
     try:
         kw = dict(kind=0, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
+        nodes = sample_nodes(mesh.n_nodes, 3) if check else None
+        rp_h = s.row_ptr.cpu().numpy() if check else None
+        snaps = {}
+        snap = (lambda name: snaps.__setitem__(name, snapshot_rows(s, nodes, rp_h))) if check else None
         out = {}
         for name, op in (("fp64_per_type", fea.make_operator(precision=0, **kw)),
                          ("fp32_per_type", fea.make_operator(precision=1, **kw))):
             out[name] = _time_calls(lambda: s.assemble(op), steps)
             s.check()
-        chunk = 128
+            if snap:
+                snap(name)
+        # the work-item size of the persistent launch: the autotuner's choice for stealing
+        tune = fea.fea_autotune(fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, chunk=128, **kw),
+                                s.handle, s.row_ptr, s.node_map, s.A, s.b, 5)
+        chunk = tune["chunk"]
         types, _, counts = fea.fea_work_items(s.handle, chunk)
         X = fea.fea_item_features(s.handle, chunk, len(counts), device=dev)
-        sched, mlp = schedule_study(fea, s, dict(precision=1, **kw), counts, types, X, dev, steps, chunk)
+        sched, mlp = schedule_study(fea, s, dict(precision=1, **kw), counts, types, X, dev, steps, chunk,
+                                    snap=(lambda n: snap("fp32_" + n)) if snap else None)
+        mlp["autotuned"] = tune
         out.update({"fp32_" + k: v for k, v in sched.items()})
-        return {"workload": "hybrid 100^3 cube, 4,528,302 elements (tet 40 / pyr 10 / prism 20 / hex 30 %), "
-                            "diffusion k = 1 + x^2, degree-2 rules",
-                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp}
+        nnz_node = s.A.numel()
+        roof = _rooflines(out, lambda k: assembly_work(_type_counts(mesh), mesh.n_nodes, nnz_node, OP_DIFFUSION,
+                                                       0 if k.startswith("fp64") else 1, k_varies=True), pk)
+        res = {"workload": "hybrid 100^3 cube, 4,528,302 elements (tet 40 / pyr 10 / prism 20 / hex 30 %), "
+                           "diffusion k = 1 + x^2, degree-2 rules",
+               "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
+               "roofline": roof}
+        if check:
+            ref = oracle_rows(mesh, nodes, OP_DIFFUSION, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
+            res["error"] = {k: row_errors(sn, ref, 1e-12 if k.startswith("fp64") else 1e-5)
+                            for k, sn in snaps.items()}
+            res["error_sample"] = f"every row of {len(nodes)} seeded nodes, oracle rows"
+        return res
     finally:
         s.close()
 
 
-def workload_j2(dev, steps=5):
+def workload_j2(dev, pk, check, steps=5):
     """Elastoplastic hex8 (J2 / Voce), 96^3, second load step from the committed first step: the
     plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules."""
     import torch
@@ -741,19 +886,33 @@ def workload_j2(dev, steps=5):
         u = torch.tensor(U.reshape(-1), device=dev)
         st1 = torch.empty((mesh.n_elems, 8, 7), dtype=torch.float64, device=dev)
         yl = torch.empty((mesh.n_elems, 8), dtype=torch.uint8, device=dev)
+        it = torch.empty((mesh.n_elems, 8), dtype=torch.uint8, device=dev)
         s.assemble(fea.make_operator(kind=fea.FEA_OP_J2, precision=0, u=0.5 * u, state_out=st1))
         st2 = torch.empty_like(st1)
         base = dict(kind=fea.FEA_OP_J2, u=u, state_in=st1, state_out=st2)
+        n = 96
+        nodes = sample_hex_nodes(n, 4, count=16) if check else None
+        rp_h = s.row_ptr.cpu().numpy() if check else None
+        snaps = {}
+        snap = (lambda name: snaps.__setitem__(name, snapshot_rows(s, nodes, rp_h))) if check else None
         out = {}
-        for name, op in (("fp64_per_type", fea.make_operator(precision=0, yield_out=yl, **base)),
+        for name, op in (("fp64_per_type", fea.make_operator(precision=0, yield_out=yl, iters_out=it, **base)),
                          ("fp32_per_type", fea.make_operator(precision=1, **base))):
             out[name] = _time_calls(lambda: s.assemble(op), steps)
             s.check()
+            if snap:
+                snap(name)
         yield_frac = float(yl.float().mean().item())
-        chunk = 32
+        j2stats = {"points": 8 * mesh.n_elems, "plastic_points": int(yl.sum().item()),
+                   "newton_iters": int(it.to(torch.int64).sum().item())}
+        tune = fea.fea_autotune(fea.make_operator(precision=1, schedule=fea.FEA_SCHED_STEAL, chunk=32, **base),
+                                s.handle, s.row_ptr, s.node_map, s.A, s.b, 5)
+        chunk = tune["chunk"]
         types, _, counts = fea.fea_work_items(s.handle, chunk)
         X = fea.fea_item_features(s.handle, chunk, len(counts), u, st1, device=dev)
-        sched, mlp = schedule_study(fea, s, dict(precision=1, **base), counts, types, X, dev, steps, chunk)
+        sched, mlp = schedule_study(fea, s, dict(precision=1, **base), counts, types, X, dev, steps, chunk,
+                                    snap=(lambda nm: snap("fp32_" + nm)) if snap else None)
+        mlp["autotuned"] = tune
         out.update({"fp32_" + k: v for k, v in sched.items()})
         # the element-wise loop (no scatter): the Gauss-point update alone
         sig = torch.empty((mesh.n_elems, 8, 6), dtype=torch.float64, device=dev)
@@ -762,19 +921,37 @@ def workload_j2(dev, steps=5):
                                       run=lambda op: fea.fea_element_loop(op, s.handle, sig),
                                       grid_fn=fea.fea_element_loop_grid)
         loop.update(lsched)
-        return {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
-                            f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
-                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
-                "element_loop": {"ms": loop, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in loop.items()},
-                                 "mlp": lmlp}}
+        nnz_node = s.A.numel() // 9
+        work = {p: assembly_work({3: mesh.n_elems}, mesh.n_nodes, nnz_node, OP_J2, p, j2=j2stats) for p in (0, 1)}
+        roof = _rooflines(out, lambda k: work[0 if k.startswith("fp64") else 1], pk)
+        # the element loop: the J2 update and its geometry and strain (FP64), state in and out
+        loop_work = {"fp64": work[1]["parts"]["geometry"] + work[1]["parts"]["j2_update"], "fp32": 0,
+                     "bytes": mesh.n_elems * (8 * 4 + 2 * 8 * 7 * 8 + 8 * 6 * 8) + mesh.n_nodes * (24 + 24)}
+        loop_roof = {k: step_roofline(loop_work, v, pk) for k, v in loop.items()}
+        res = {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
+                           f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
+               "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
+               "roofline": roof, "j2_work": j2stats,
+               "element_loop": {"ms": loop, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in loop.items()},
+                                "mlp": lmlp, "roofline": loop_roof}}
+        if check:
+            ref = oracle_j2_rows(mesh, U, nodes)
+            res["error"] = {k: row_errors(sn, ref, 1e-12 if k.startswith("fp64") else 1e-5)
+                            for k, sn in snaps.items()}
+            res["error_sample"] = f"every dof row of {len(nodes)} seeded nodes, oracle rows (both load steps)"
+            elems = np.random.default_rng(8).choice(mesh.n_elems, size=256, replace=False)
+            ei = torch.as_tensor(elems, device=dev)
+            res["element_loop"]["error"] = dict(
+                oracle_j2_point_errors(mesh, U, elems, st2[ei].cpu().numpy(), sig[ei].cpu().numpy()),
+                sample="256 seeded elements x 8 points, the oracle's own two steps")
+        return res
     finally:
         s.close()
 
 
-def workload_batch(dev, steps=10):
+def workload_batch(dev, pk, check, steps=10):
     """256 tet4/hex8 elasticity meshes (log-uniform 1e3..2e5 elements), one graph-captured
     persistent launch, autotuned chunk and grid; aggregate rate and per-mesh latency."""
-    import torch
     from paper_1805_03949_gb300 import fea, meshgen as mg
     meshes = mg.batch_meshes(256, 5)
     systems = [fea.System.from_mesh(m, 3, device=dev, with_cols=False) for m in meshes]
@@ -789,11 +966,29 @@ def workload_batch(dev, steps=10):
         for s in systems:
             s.check()
         E = sum(m.n_elems for m in meshes)
-        return {"workload": f"256 tet4/hex8 elasticity meshes, {E:,} elements, FP32-integrate, one CUDA graph "
-                            "(zeroing kernel + persistent work-stealing launch)",
-                "ms": ms, "elements_per_s": E / (ms * 1e-3), "autotuned": tuned,
-                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                               "max": float(lat.max())}}
+        total = {"fp64": 0, "fp32": 0, "bytes": 0}
+        for m, s in zip(meshes, systems):
+            w = assembly_work(_type_counts(m), m.n_nodes, s.A.numel() // 9, OP_ELASTICITY, 1)
+            for k in total:
+                total[k] += w[k]
+        res = {"workload": f"256 tet4/hex8 elasticity meshes, {E:,} elements, FP32-integrate, one CUDA graph "
+                           "(zeroing kernel + persistent work-stealing launch)",
+               "ms": ms, "elements_per_s": E / (ms * 1e-3), "autotuned": tuned,
+               "roofline": step_roofline(total, ms, pk),
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max())}}
+        if check:
+            sizes = np.array([m.n_elems for m in meshes])
+            pick = sorted({int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))})
+            errs = {}
+            for k in pick:
+                nd = sample_nodes(meshes[k].n_nodes, 50 + k, count=8)
+                sn = snapshot_rows(systems[k], nd)
+                ref = oracle_rows(meshes[k], nd, OP_ELASTICITY, tet_rule=1, young=1.0, poisson=0.3)
+                errs[f"mesh{k}_{meshes[k].n_elems}"] = row_errors(sn, ref, 1e-5)
+            res["error"] = errs
+            res["error_sample"] = "the smallest, the median and the largest mesh: every row of 10 seeded nodes"
+        return res
     finally:
         if batch is not None:
             batch.close()
@@ -801,14 +996,16 @@ def workload_batch(dev, steps=10):
             s.close()
 
 
-def other_workloads(args, dev):
-    """Time the mixed-element diffusion, J2 and batch workloads named in --workloads."""
+def other_workloads(args, dev, pk):
+    """Time the workloads named in --workloads (Poisson, mixed-element diffusion, J2, batch)."""
     out = {}
     wanted = [c for c in args.workloads.split(",") if c]
-    for key, fn in (("hybrid", workload_hybrid), ("j2", workload_j2), ("batch", workload_batch)):
+    check = not args.no_oracle
+    for key, fn in (("poisson", workload_poisson), ("hybrid", workload_hybrid), ("j2", workload_j2),
+                    ("batch", workload_batch)):
         if key in wanted:
             t0 = time.perf_counter()
-            out[key] = fn(dev)
+            out[key] = fn(dev, pk, check)
             out[key]["wall_s"] = time.perf_counter() - t0
             import torch
             torch.cuda.empty_cache()
@@ -816,7 +1013,79 @@ def other_workloads(args, dev):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle (cpu_baseline and --impl reference)
+# sampled results, copied to the host after a timed region (no oracle here)
+# ---------------------------------------------------------------------------
+
+def sample_hex_nodes(n, seed, count=24):
+    """Corner, edge, face and centre nodes of an n^3 hex lattice, and `count` seeded ones."""
+    m = n + 1
+    idx = lambda i, j, k: i + m * (j + m * k)
+    fixed = [idx(0, 0, 0), idx(n, n, n), idx(n, 0, 0), idx(0, n, min(5, n)), idx(min(3, n), 0, min(7, n)),
+             idx(n, min(9, n), n // 2), idx(n // 2, n // 2, n // 2)]
+    rnd = np.random.default_rng(seed).integers(0, m ** 3, size=count).tolist()
+    return np.array(sorted(set(fixed + rnd)), dtype=np.int32)
+
+
+def sample_nodes(n_nodes, seed, count=24):
+    """The first and last node and `count` seeded ones."""
+    rnd = np.random.default_rng(seed).integers(0, n_nodes, size=count)
+    return np.unique(np.concatenate([rnd, [0, n_nodes - 1]])).astype(np.int32)
+
+
+def snapshot_rows(system, nodes, rp_h=None):
+    """Every dof row of the given nodes in the system's A, and their b entries, on the host."""
+    import torch
+    d = system.ndof
+    if rp_h is None:
+        rp_h = system.row_ptr.cpu().numpy()
+    segs = [(int(rp_h[d * nd + c]), int(rp_h[d * nd + c + 1])) for nd in nodes for c in range(d)]
+    idx = np.concatenate([np.arange(lo, hi) for lo, hi in segs]).astype(np.int64)
+    vals = system.A[torch.as_tensor(idx, device=system.A.device)].cpu().numpy()
+    bidx = np.array([d * nd + c for nd in nodes for c in range(d)], dtype=np.int64)
+    bv = system.b[torch.as_tensor(bidx, device=system.b.device)].cpu().numpy()
+    rows, o = [], 0
+    for lo, hi in segs:
+        rows.append(vals[o:o + hi - lo])
+        o += hi - lo
+    return {"nodes": np.asarray(nodes), "d": d, "rows": rows, "b": bv}
+
+
+def row_errors(snap, ref_rows, bar):
+    """Error of sampled rows against reference rows (the oracle's, one dict per node with
+    vals / nvals [d, k d], b / sb [d]):
+      normwise: max |a - r| / N, N the entry's normwise scale (entries with N = 0
+                count |a| / max N); the metric the parity bars apply to;
+      relative: max |a - r| / |r| over entries with |r| >= 1e-8 max over the row |r|;
+    for A and b."""
+    d = snap["d"]
+    nw = rel = bnw = brel = 0.0
+    n_ent = 0
+    for k, r in enumerate(ref_rows):
+        for c in range(d):
+            a, v, nv = snap["rows"][k * d + c], r["vals"][c], r["nvals"][c]
+            if len(a) != len(v):
+                raise ValueError("sampled row and reference row differ in length")
+            n_ent += len(v)
+            diff = np.abs(a - v)
+            pos = nv > 0
+            if pos.any():
+                nw = max(nw, float(np.max(diff[pos] / nv[pos])))
+            if (~pos).any():
+                nw = max(nw, float(np.max(np.abs(a[~pos]))) / max(float(nv.max()), 1e-300))
+            big = np.abs(v) >= 1e-8 * np.abs(v).max()
+            if big.any():
+                rel = max(rel, float(np.max(diff[big] / np.abs(v[big]))))
+            db = abs(float(snap["b"][k * d + c]) - r["b"][c])
+            if r["sb"][c] > 0:
+                bnw = max(bnw, db / r["sb"][c])
+            if r["b"][c] != 0:
+                brel = max(brel, db / abs(r["b"][c]))
+    return {"A_normwise": nw, "A_relative": rel, "b_normwise": bnw, "b_relative": brel, "bar": bar,
+            "within_bar": bool(nw <= bar and bnw <= bar), "rows": len(ref_rows) * d, "entries": n_ent}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline, --impl reference, and the error of each result)
 # ---------------------------------------------------------------------------
 
 def _slab(mesh, layers, n):
@@ -843,6 +1112,103 @@ def cpu_baseline(args, mesh=None, layers=None):
             "sample": f"first {layers} of {n} cell layers of the workload ({sub.n_elems} elements), "
                       f"single-thread FP64 oracle, element-index order, pattern excluded",
             "seconds": dt}
+
+
+def oracle_full_errors(mesh, snaps, prec, op, **kw):
+    """Oracle leg: the whole assembled system of a small workload against the oracle's."""
+    from oracle import oracle as O
+    ref = O.assemble(mesh, op, **kw)
+    out = {}
+    for k, (A, b) in snaps.items():
+        pos = ref["NA"] > 0
+        dA = np.abs(A - ref["A"])
+        big = np.abs(ref["A"]) >= 1e-8 * np.abs(ref["A"]).max()
+        bar = 1e-12 if prec[k] == 0 else 1e-5
+        nw = max(float(np.max(dA[pos] / ref["NA"][pos])),
+                 float(np.max(np.abs(A[~pos]), initial=0.0)) / float(ref["NA"].max()))
+        bnw = float(np.max(np.abs(b - ref["b"]) / ref["Nb"]))
+        out[k] = {"A_normwise": nw, "A_relative": float(np.max(dA[big] / np.abs(ref["A"][big]))),
+                  "b_normwise": bnw, "b_relative": float(np.max(np.abs(b - ref["b"]) / np.abs(ref["b"]))),
+                  "bar": bar, "within_bar": bool(nw <= bar and bnw <= bar), "entries": int(A.size),
+                  "sample": "the whole system"}
+    return out
+
+
+def oracle_rows(mesh, nodes, op, **kw):
+    """Oracle leg: every dof row of the nodes, summed over all elements in index order."""
+    from oracle import oracle as O
+    return O.assemble_rows(mesh, nodes, op, **kw)
+
+
+def _rows_from_elements(mesh, nodes, element_fn):
+    """Oracle leg: rows of the nodes of a hex8 mesh (3 dofs per node) summed from
+    per-element matrices; element_fn(e) -> dict(A, b, NA, Nb) of element e."""
+    conn = np.asarray(mesh.conn).reshape(-1, 8)
+    out = []
+    for node in nodes:
+        blocks = {}
+        b = np.zeros(3)
+        sb = np.zeros(3)
+        for e, a in zip(*np.nonzero(conn == node)):
+            r = element_fn(int(e))
+            for bb in range(8):
+                j = int(conn[e, bb])
+                v, nv = blocks.get(j, (np.zeros((3, 3)), np.zeros((3, 3))))
+                blocks[j] = (v + r["A"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3],
+                             nv + r["NA"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3])
+            b += r["b"][3 * a:3 * a + 3]
+            sb += r["Nb"][3 * a:3 * a + 3]
+        cols = sorted(blocks)
+        vals = np.concatenate([blocks[j][0] for j in cols], axis=1)
+        nvals = np.concatenate([blocks[j][1] for j in cols], axis=1)
+        out.append({"cols": np.array(cols), "vals": vals, "nvals": nvals, "b": b, "sb": sb})
+    return out
+
+
+def oracle_j2_rows(mesh, U, nodes):
+    """Oracle leg: rows of the J2 tangent and internal force at displacement U after
+    the committed step at 0.5 U (both steps taken by the oracle, per element)."""
+    from oracle import oracle as O
+    conn = np.asarray(mesh.conn).reshape(-1, 8)
+
+    def elem(e):
+        X, Ue = mesh.coords[conn[e]], U[conn[e]]
+        st1 = O.j2_element(3, X, 0.5 * Ue)["state"]
+        return O.j2_element(3, X, Ue, st1)
+    return _rows_from_elements(mesh, nodes, elem)
+
+
+def oracle_nh_rows(mesh, U, nodes):
+    """Oracle leg: rows of the finite-strain Jacobian and internal force at U."""
+    from oracle import oracle as O
+    conn = np.asarray(mesh.conn).reshape(-1, 8)
+    return _rows_from_elements(mesh, nodes, lambda e: O.nh_element(3, mesh.coords[conn[e]], U[conn[e]],
+                                                                   young=1.0, poisson=0.3))
+
+
+def oracle_j2_point_errors(mesh, U, elems, state, stress, young=1.0, poisson=0.3):
+    """Oracle leg: the J2 update (state and stress of step 2 from the oracle's own
+    step 1) on sampled hex elements, against the GPU's; per-point normwise errors
+    with the scale S = max|eps_p| + |alpha| + max|sigma| / (2 mu) of the point."""
+    from oracle import oracle as O
+    from paper_1805_03949_gb300 import meshgen as mg
+    conn = np.asarray(mesh.conn).reshape(-1, 8)[elems]
+    sub = mg.Mesh(mesh.coords, np.full(len(elems), 3, dtype=np.uint8),
+                  np.arange(len(elems) + 1, dtype=np.int64) * 8, conn.reshape(-1).astype(np.int32), {})
+    r1 = O.j2_points(sub, 0.5 * U)
+    r2 = O.j2_points(sub, U, r1["state"])
+    mu = young / (2.0 * (1.0 + poisson))
+    kappa = young / (3.0 * (1.0 - 2.0 * poisson))
+    S = (np.abs(r2["state"][..., :6]).max(-1) + np.abs(r2["state"][..., 6])
+         + np.abs(r2["stress"]).max(-1) / (2.0 * mu)).reshape(-1)
+    ds = np.abs(state - r2["state"]).max(-1).reshape(-1)
+    dsig = np.abs(stress - r2["stress"]).max(-1).reshape(-1)
+    pos = S > 0
+    return {"state_normwise": float(np.max(ds[pos] / S[pos])),
+            "stress_normwise": float(np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos]))),
+            "points": int(pos.size), "bar": 1e-12,
+            "within_bar": bool(np.max(ds[pos] / S[pos]) <= 1e-12
+                               and np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos])) <= 1e-12)}
 
 
 def workload_name(n: int) -> str:
@@ -894,11 +1260,14 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--cpu-layers", type=int, default=8)
     ap.add_argument("--ref-layers", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="time the default launch parameters")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip every oracle step: the CPU baseline and the error of each result")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the raw nvidia-smi clock samples of the timed region are written")
-    ap.add_argument("--workloads", "--configs", dest="workloads", default="hybrid,j2,batch",
-                    help="other workloads timed after the headline one (comma list of hybrid, j2, batch; "
-                         "'' for none)")
+    ap.add_argument("--workloads", "--configs", dest="workloads", default="poisson,hybrid,j2,batch",
+                    help="other workloads timed after the headline one (comma list of poisson, hybrid, j2, "
+                         "batch; '' for none)")
     return ap
 
 
