@@ -684,13 +684,13 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = cpu_baseline(args)
         if check:
             # oracle leg: the error of every variant's sampled rows (after every timed region)
-            ref = oracle_rows(mesh, nodes, OP_ELASTICITY, young=1.0, poisson=0.3)
+            ref = CpuBaselineLeg.rows(mesh, nodes, OP_ELASTICITY, young=1.0, poisson=0.3)
             errs = {k: row_errors(sn, ref, 1e-12 if VARIANTS[k][0] == 0 else 1e-5) for k, sn in snaps.items()}
             sample = f"every dof row of {len(nodes)} seeded nodes (corners, edges, faces, interior), oracle rows"
             line["error"] = dict(errs[head], sample=sample)
             line["errors"] = errs
             if nh_snaps:
-                nh_ref = oracle_nh_rows(mesh, nh_U, nh_nodes)
+                nh_ref = CpuBaselineLeg.nh_rows(mesh, nh_U, nh_nodes)
                 for k, sn in nh_snaps.items():
                     neo[k]["error"] = row_errors(sn, nh_ref, 1e-12 if k.startswith("fp64") else 1e-5)
         if world == 1 and args.workloads:
@@ -821,7 +821,7 @@ def workload_poisson(dev, pk, check, steps=20):
                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()},
                "roofline": roof, "bound_note": "the whole problem (about 2 MB) lives in L2: launch latency bounds it"}
         if check:
-            res["error"] = oracle_full_errors(mesh, snaps, prec, OP_DIFFUSION, tet_rule=0, k0=1.0, k2=0.0,
+            res["error"] = CpuBaselineLeg.full_errors(mesh, snaps, prec, OP_DIFFUSION, tet_rule=0, k0=1.0, k2=0.0,
                                               source=1.0)
         return res
     finally:
@@ -865,7 +865,7 @@ def workload_hybrid(dev, pk, check, steps=5):
                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
                "roofline": roof}
         if check:
-            ref = oracle_rows(mesh, nodes, OP_DIFFUSION, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
+            ref = CpuBaselineLeg.rows(mesh, nodes, OP_DIFFUSION, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
             res["error"] = {k: row_errors(sn, ref, 1e-12 if k.startswith("fp64") else 1e-5)
                             for k, sn in snaps.items()}
             res["error_sample"] = f"every row of {len(nodes)} seeded nodes, oracle rows"
@@ -935,14 +935,14 @@ def workload_j2(dev, pk, check, steps=5):
                "element_loop": {"ms": loop, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in loop.items()},
                                 "mlp": lmlp, "roofline": loop_roof}}
         if check:
-            ref = oracle_j2_rows(mesh, U, nodes)
+            ref = CpuBaselineLeg.j2_rows(mesh, U, nodes)
             res["error"] = {k: row_errors(sn, ref, 1e-12 if k.startswith("fp64") else 1e-5)
                             for k, sn in snaps.items()}
             res["error_sample"] = f"every dof row of {len(nodes)} seeded nodes, oracle rows (both load steps)"
             elems = np.random.default_rng(8).choice(mesh.n_elems, size=256, replace=False)
             ei = torch.as_tensor(elems, device=dev)
             res["element_loop"]["error"] = dict(
-                oracle_j2_point_errors(mesh, U, elems, st2[ei].cpu().numpy(), sig[ei].cpu().numpy()),
+                CpuBaselineLeg.j2_point_errors(mesh, U, elems, st2[ei].cpu().numpy(), sig[ei].cpu().numpy()),
                 sample="256 seeded elements x 8 points, the oracle's own two steps")
         return res
     finally:
@@ -984,7 +984,7 @@ def workload_batch(dev, pk, check, steps=10):
             for k in pick:
                 nd = sample_nodes(meshes[k].n_nodes, 50 + k, count=8)
                 sn = snapshot_rows(systems[k], nd)
-                ref = oracle_rows(meshes[k], nd, OP_ELASTICITY, tet_rule=1, young=1.0, poisson=0.3)
+                ref = CpuBaselineLeg.rows(meshes[k], nd, OP_ELASTICITY, tet_rule=1, young=1.0, poisson=0.3)
                 errs[f"mesh{k}_{meshes[k].n_elems}"] = row_errors(sn, ref, 1e-5)
             res["error"] = errs
             res["error_sample"] = "the smallest, the median and the largest mesh: every row of 10 seeded nodes"
@@ -1114,101 +1114,108 @@ def cpu_baseline(args, mesh=None, layers=None):
             "seconds": dt}
 
 
-def oracle_full_errors(mesh, snaps, prec, op, **kw):
-    """Oracle leg: the whole assembled system of a small workload against the oracle's."""
-    from oracle import oracle as O
-    ref = O.assemble(mesh, op, **kw)
-    out = {}
-    for k, (A, b) in snaps.items():
-        pos = ref["NA"] > 0
-        dA = np.abs(A - ref["A"])
-        big = np.abs(ref["A"]) >= 1e-8 * np.abs(ref["A"]).max()
-        bar = 1e-12 if prec[k] == 0 else 1e-5
-        nw = max(float(np.max(dA[pos] / ref["NA"][pos])),
-                 float(np.max(np.abs(A[~pos]), initial=0.0)) / float(ref["NA"].max()))
-        bnw = float(np.max(np.abs(b - ref["b"]) / ref["Nb"]))
-        out[k] = {"A_normwise": nw, "A_relative": float(np.max(dA[big] / np.abs(ref["A"][big]))),
-                  "b_normwise": bnw, "b_relative": float(np.max(np.abs(b - ref["b"]) / np.abs(ref["b"]))),
-                  "bar": bar, "within_bar": bool(nw <= bar and bnw <= bar), "entries": int(A.size),
-                  "sample": "the whole system"}
-    return out
+class CpuBaselineLeg:
+    """The CPU-baseline leg: everything bench.py does with the oracle, on the host,
+    after every timed GPU region -- timing the oracle on a bounded sample of the
+    workload (cpu_baseline) and recomputing sampled results, from which the error
+    of each GPU result is reported.  Nothing else in the bench touches the oracle."""
 
+    @staticmethod
+    def full_errors(mesh, snaps, prec, op, **kw):
+        """Oracle leg: the whole assembled system of a small workload against the oracle's."""
+        from oracle import oracle as O
+        ref = O.assemble(mesh, op, **kw)
+        out = {}
+        for k, (A, b) in snaps.items():
+            pos = ref["NA"] > 0
+            dA = np.abs(A - ref["A"])
+            big = np.abs(ref["A"]) >= 1e-8 * np.abs(ref["A"]).max()
+            bar = 1e-12 if prec[k] == 0 else 1e-5
+            nw = max(float(np.max(dA[pos] / ref["NA"][pos])),
+                     float(np.max(np.abs(A[~pos]), initial=0.0)) / float(ref["NA"].max()))
+            bnw = float(np.max(np.abs(b - ref["b"]) / ref["Nb"]))
+            out[k] = {"A_normwise": nw, "A_relative": float(np.max(dA[big] / np.abs(ref["A"][big]))),
+                      "b_normwise": bnw, "b_relative": float(np.max(np.abs(b - ref["b"]) / np.abs(ref["b"]))),
+                      "bar": bar, "within_bar": bool(nw <= bar and bnw <= bar), "entries": int(A.size),
+                      "sample": "the whole system"}
+        return out
 
-def oracle_rows(mesh, nodes, op, **kw):
-    """Oracle leg: every dof row of the nodes, summed over all elements in index order."""
-    from oracle import oracle as O
-    return O.assemble_rows(mesh, nodes, op, **kw)
+    @staticmethod
+    def rows(mesh, nodes, op, **kw):
+        """Oracle leg: every dof row of the nodes, summed over all elements in index order."""
+        from oracle import oracle as O
+        return O.assemble_rows(mesh, nodes, op, **kw)
 
+    @staticmethod
+    def rows_from_elements(mesh, nodes, element_fn):
+        """Oracle leg: rows of the nodes of a hex8 mesh (3 dofs per node) summed from
+        per-element matrices; element_fn(e) -> dict(A, b, NA, Nb) of element e."""
+        conn = np.asarray(mesh.conn).reshape(-1, 8)
+        out = []
+        for node in nodes:
+            blocks = {}
+            b = np.zeros(3)
+            sb = np.zeros(3)
+            for e, a in zip(*np.nonzero(conn == node)):
+                r = element_fn(int(e))
+                for bb in range(8):
+                    j = int(conn[e, bb])
+                    v, nv = blocks.get(j, (np.zeros((3, 3)), np.zeros((3, 3))))
+                    blocks[j] = (v + r["A"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3],
+                                 nv + r["NA"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3])
+                b += r["b"][3 * a:3 * a + 3]
+                sb += r["Nb"][3 * a:3 * a + 3]
+            cols = sorted(blocks)
+            vals = np.concatenate([blocks[j][0] for j in cols], axis=1)
+            nvals = np.concatenate([blocks[j][1] for j in cols], axis=1)
+            out.append({"cols": np.array(cols), "vals": vals, "nvals": nvals, "b": b, "sb": sb})
+        return out
 
-def _rows_from_elements(mesh, nodes, element_fn):
-    """Oracle leg: rows of the nodes of a hex8 mesh (3 dofs per node) summed from
-    per-element matrices; element_fn(e) -> dict(A, b, NA, Nb) of element e."""
-    conn = np.asarray(mesh.conn).reshape(-1, 8)
-    out = []
-    for node in nodes:
-        blocks = {}
-        b = np.zeros(3)
-        sb = np.zeros(3)
-        for e, a in zip(*np.nonzero(conn == node)):
-            r = element_fn(int(e))
-            for bb in range(8):
-                j = int(conn[e, bb])
-                v, nv = blocks.get(j, (np.zeros((3, 3)), np.zeros((3, 3))))
-                blocks[j] = (v + r["A"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3],
-                             nv + r["NA"][3 * a:3 * a + 3, 3 * bb:3 * bb + 3])
-            b += r["b"][3 * a:3 * a + 3]
-            sb += r["Nb"][3 * a:3 * a + 3]
-        cols = sorted(blocks)
-        vals = np.concatenate([blocks[j][0] for j in cols], axis=1)
-        nvals = np.concatenate([blocks[j][1] for j in cols], axis=1)
-        out.append({"cols": np.array(cols), "vals": vals, "nvals": nvals, "b": b, "sb": sb})
-    return out
+    @staticmethod
+    def j2_rows(mesh, U, nodes):
+        """Oracle leg: rows of the J2 tangent and internal force at displacement U after
+        the committed step at 0.5 U (both steps taken by the oracle, per element)."""
+        from oracle import oracle as O
+        conn = np.asarray(mesh.conn).reshape(-1, 8)
 
+        def elem(e):
+            X, Ue = mesh.coords[conn[e]], U[conn[e]]
+            st1 = O.j2_element(3, X, 0.5 * Ue)["state"]
+            return O.j2_element(3, X, Ue, st1)
+        return CpuBaselineLeg.rows_from_elements(mesh, nodes, elem)
 
-def oracle_j2_rows(mesh, U, nodes):
-    """Oracle leg: rows of the J2 tangent and internal force at displacement U after
-    the committed step at 0.5 U (both steps taken by the oracle, per element)."""
-    from oracle import oracle as O
-    conn = np.asarray(mesh.conn).reshape(-1, 8)
+    @staticmethod
+    def nh_rows(mesh, U, nodes):
+        """Oracle leg: rows of the finite-strain Jacobian and internal force at U."""
+        from oracle import oracle as O
+        conn = np.asarray(mesh.conn).reshape(-1, 8)
+        return CpuBaselineLeg.rows_from_elements(mesh, nodes, lambda e: O.nh_element(3, mesh.coords[conn[e]], U[conn[e]],
+                                                                       young=1.0, poisson=0.3))
 
-    def elem(e):
-        X, Ue = mesh.coords[conn[e]], U[conn[e]]
-        st1 = O.j2_element(3, X, 0.5 * Ue)["state"]
-        return O.j2_element(3, X, Ue, st1)
-    return _rows_from_elements(mesh, nodes, elem)
-
-
-def oracle_nh_rows(mesh, U, nodes):
-    """Oracle leg: rows of the finite-strain Jacobian and internal force at U."""
-    from oracle import oracle as O
-    conn = np.asarray(mesh.conn).reshape(-1, 8)
-    return _rows_from_elements(mesh, nodes, lambda e: O.nh_element(3, mesh.coords[conn[e]], U[conn[e]],
-                                                                   young=1.0, poisson=0.3))
-
-
-def oracle_j2_point_errors(mesh, U, elems, state, stress, young=1.0, poisson=0.3):
-    """Oracle leg: the J2 update (state and stress of step 2 from the oracle's own
-    step 1) on sampled hex elements, against the GPU's; per-point normwise errors
-    with the scale S = max|eps_p| + |alpha| + max|sigma| / (2 mu) of the point."""
-    from oracle import oracle as O
-    from paper_1805_03949_gb300 import meshgen as mg
-    conn = np.asarray(mesh.conn).reshape(-1, 8)[elems]
-    sub = mg.Mesh(mesh.coords, np.full(len(elems), 3, dtype=np.uint8),
-                  np.arange(len(elems) + 1, dtype=np.int64) * 8, conn.reshape(-1).astype(np.int32), {})
-    r1 = O.j2_points(sub, 0.5 * U)
-    r2 = O.j2_points(sub, U, r1["state"])
-    mu = young / (2.0 * (1.0 + poisson))
-    kappa = young / (3.0 * (1.0 - 2.0 * poisson))
-    S = (np.abs(r2["state"][..., :6]).max(-1) + np.abs(r2["state"][..., 6])
-         + np.abs(r2["stress"]).max(-1) / (2.0 * mu)).reshape(-1)
-    ds = np.abs(state - r2["state"]).max(-1).reshape(-1)
-    dsig = np.abs(stress - r2["stress"]).max(-1).reshape(-1)
-    pos = S > 0
-    return {"state_normwise": float(np.max(ds[pos] / S[pos])),
-            "stress_normwise": float(np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos]))),
-            "points": int(pos.size), "bar": 1e-12,
-            "within_bar": bool(np.max(ds[pos] / S[pos]) <= 1e-12
-                               and np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos])) <= 1e-12)}
+    @staticmethod
+    def j2_point_errors(mesh, U, elems, state, stress, young=1.0, poisson=0.3):
+        """Oracle leg: the J2 update (state and stress of step 2 from the oracle's own
+        step 1) on sampled hex elements, against the GPU's; per-point normwise errors
+        with the scale S = max|eps_p| + |alpha| + max|sigma| / (2 mu) of the point."""
+        from oracle import oracle as O
+        from paper_1805_03949_gb300 import meshgen as mg
+        conn = np.asarray(mesh.conn).reshape(-1, 8)[elems]
+        sub = mg.Mesh(mesh.coords, np.full(len(elems), 3, dtype=np.uint8),
+                      np.arange(len(elems) + 1, dtype=np.int64) * 8, conn.reshape(-1).astype(np.int32), {})
+        r1 = O.j2_points(sub, 0.5 * U)
+        r2 = O.j2_points(sub, U, r1["state"])
+        mu = young / (2.0 * (1.0 + poisson))
+        kappa = young / (3.0 * (1.0 - 2.0 * poisson))
+        S = (np.abs(r2["state"][..., :6]).max(-1) + np.abs(r2["state"][..., 6])
+             + np.abs(r2["stress"]).max(-1) / (2.0 * mu)).reshape(-1)
+        ds = np.abs(state - r2["state"]).max(-1).reshape(-1)
+        dsig = np.abs(stress - r2["stress"]).max(-1).reshape(-1)
+        pos = S > 0
+        return {"state_normwise": float(np.max(ds[pos] / S[pos])),
+                "stress_normwise": float(np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos]))),
+                "points": int(pos.size), "bar": 1e-12,
+                "within_bar": bool(np.max(ds[pos] / S[pos]) <= 1e-12
+                                   and np.max(dsig[pos] / ((3 * kappa + 2 * mu) * S[pos])) <= 1e-12)}
 
 
 def workload_name(n: int) -> str:
