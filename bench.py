@@ -43,11 +43,12 @@ NOMINAL_FP32_TFLOPS = 80.5     # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 METRIC = "assembled elements/s and % roofline vs plain atomic FP64 assembly, same GB300"
 
 # DRAM bytes (read + write) of one launch of a kernel at the 128^3 workload: an
-# ncu capture of the 64^3 case (same kernel and launch shape, inputs larger than
-# L2) scaled by the element count, which its traffic grows with.  Remove an
-# entry whenever its kernel changes.
-TRAFFIC_BYTES = {"k_assemble_tile": 8.0 * (612.967936e6 + 465.030656e6),
-                 "k_block_pipe": 8.0 * (415.417088e6 + 575.375360e6)}
+# ncu capture of the 64^3 case in the same configuration (inputs larger than
+# L2), scaled by the element count, which the traffic grows with.  Keyed by
+# (kernel, elements per block, producer warps) for the block-task kernel, whose
+# traffic depends on its configuration; remove an entry whenever its kernel
+# changes, and a configuration without an entry reports no traffic.
+TRAFFIC_BYTES = {}
 
 # the kernel each variant spends its step in
 DOMINANT_KERNEL = {"atomic": "k_assemble_tile", "color": "k_assemble_tile (one launch per color)",
@@ -427,6 +428,10 @@ def run_ours(args, rank, world, local_rank):
     snaps = {}
     if args.block_nodes:
         fea.fea_mesh_set_rows_block(sysm.handle, args.block_nodes)
+    if args.block_elems:
+        fea.fea_mesh_set_block_elems(sysm.handle, args.block_elems)
+    if args.pipe_split:
+        fea.fea_mesh_set_pipe_split(sysm.handle, args.pipe_split)
     if args.only:
         keep = set(args.only.split(",")) | {"fp64_atomic"}
         variants = {k: v for k, v in variants.items() if k in keep}
@@ -441,7 +446,8 @@ def run_ours(args, rank, world, local_rank):
         sysm.assemble(op)                            # first call builds any plan the variant needs
         sysm.check()
         plan_s[name] = time.perf_counter() - t_first
-        if name in TUNED_VARIANTS and not args.no_tune and not (name.endswith("rows") and args.block_nodes):
+        fixed = (name.endswith("rows") and args.block_nodes) or (name.endswith("block") and args.block_elems)
+        if name in TUNED_VARIANTS and not args.no_tune and not fixed:
             # block sizes, the producer/consumer split, subdomain size: timed by the engine's autotuner
             t0 = time.perf_counter()
             tuned[name] = fea.fea_autotune(op, sysm.handle, sysm.row_ptr, sysm.node_map, sysm.A, sysm.b, 5)
@@ -633,8 +639,13 @@ def run_ours(args, rank, world, local_rank):
             else:
                 roof = {"bound": "hbm", "achieved": by / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                         "peak_source": peak_kind, "algorithmic_bytes": by}
+        kcfg = (k_name.split()[0],)
+        if kind == "block":
+            t = tuned.get(head, {})
+            kcfg += (t.get("block_elems", args.block_elems or 64), t.get("producer_warps", args.pipe_split or 6))
         roof.update(frac=roof["achieved"] / roof["peak"], kernel=k_name, kernel_ms=k_ms,
-                    traffic=TRAFFIC_BYTES.get(k_name.split()[0]) if args.n == 128 else None)
+                    traffic=TRAFFIC_BYTES.get(kcfg) if args.n == 128 else None,
+                    kernel_config=list(kcfg[1:]) if len(kcfg) > 1 else None)
         if "peak_nominal" in roof:
             roof["frac_nominal"] = roof["achieved"] / roof["peak_nominal"]
         line = {
@@ -750,9 +761,10 @@ def _time_calls(fn, steps, warmup=2):
 
 def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, grid_fn=None, snap=None):
     """Persistent schedules of one workload: work stealing (whose per-item timings train the
-    cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, and
-    the same queues with stealing as the fallback once a CTA's own queue is empty.  snap(name)
-    is called after each schedule's timed calls (results sampled for the error report)."""
+    cost model), static LPT queues packed by the MLP's predictions or by Gauss-point weights, the
+    same queues with stealing as the fallback once a CTA's own queue is empty, and stealing in
+    predicted-cost order (largest first).  snap(name) is called after each schedule's timed calls
+    (results sampled for the error report)."""
     import torch
     from paper_1805_03949_gb300 import meshgen as mg
     run = run or s.assemble
@@ -782,10 +794,19 @@ def schedule_study(fea, s, base, counts, types, X, dev, steps, chunk, run=None, 
             out[f"{name}_queues{suffix}"] = _time_calls(lambda: run(op), steps)
             s.check()
             snap(f"{name}_queues{suffix}")
+        # list scheduling in predicted-cost order: stealing takes the items
+        # largest first (LPT order), so the tail holds the smallest ones
+        order = torch.tensor(np.argsort(-cost, kind="stable").astype(np.int32), device=dev)
+        op = fea.make_operator(schedule=fea.FEA_SCHED_STEAL, chunk=chunk, queue=order, **base)
+        out[f"{name}_ordered_steal"] = _time_calls(lambda: run(op), steps)
+        s.check()
+        snap(f"{name}_ordered_steal")
     return out, {"train_loss": loss, "train_s": train_s, "epochs": 600, "items": len(counts), "chunk": chunk,
-                 "grid": grid,
+                 "grid": grid, "items_per_cta": len(counts) / grid,
                  "gain_static": out["gauss_points_queues"] / out["mlp_queues"] - 1.0,
-                 "gain_with_steal": out["gauss_points_queues_steal"] / out["mlp_queues_steal"] - 1.0}
+                 "gain_with_steal": out["gauss_points_queues_steal"] / out["mlp_queues_steal"] - 1.0,
+                 "gain_ordered_vs_gauss_points": out["gauss_points_ordered_steal"] / out["mlp_ordered_steal"] - 1.0,
+                 "gain_ordered_vs_steal": out["persistent_steal"] / out["mlp_ordered_steal"] - 1.0}
 
 
 def _type_counts(mesh):
@@ -1263,6 +1284,9 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--variant", default="", help="headline variant (default: the fastest fp32 one)")
     ap.add_argument("--only", default="", help="comma list of variants to time (fp64_atomic always)")
     ap.add_argument("--block-nodes", type=int, default=0)
+    ap.add_argument("--block-elems", type=int, default=0,
+                    help="elements per block of the block-task scatter (no autotuning of the block-task variant)")
+    ap.add_argument("--pipe-split", type=int, default=0, help="producer warps of the pipelined block-task kernel")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--cpu-layers", type=int, default=8)
     ap.add_argument("--ref-layers", type=int, default=2)

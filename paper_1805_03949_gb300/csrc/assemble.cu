@@ -643,6 +643,15 @@ __device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams
     tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC>(sm, c_rules[SLOT], P, e0, end);
 }
 
+// One item of the any-type kernel, not inlined: the switch over five inlined
+// tile bodies made ptxas allocate well above the largest body's registers
+// (FP32 diffusion: 128 against 72), which cut the all-type launch's
+// occupancy; a call keeps the kernel near the largest body (96).
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
+__device__ __noinline__ void persist_item_call(unsigned char* raw, const AsmParams& P, int64_t first, int64_t end) {
+  persist_item<TYPE, SLOT, OP, PREC, SPLIT>(raw, P, first, end);
+}
+
 // ONLY >= 0: every item uses that rule slot (a single-type mesh), so the
 // kernel holds one tile body and its register budget; -1: any element type
 template <int OP, int PREC, int ONLY>
@@ -665,21 +674,21 @@ __global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ Pers
     } else if (A.tab) {
       const AsmParams& P = A.tab[it.entry];
       switch (A.tab_slot[it.entry]) {
-        case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
-        case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
-        case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
-        case kRulePrism6: persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
-        default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
+        case kRuleTet1: persist_item_call<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRuleTet4: persist_item_call<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRulePyr8: persist_item_call<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, P, first, end); break;
+        case kRulePrism6: persist_item_call<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, P, first, end); break;
+        default: persist_item_call<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, P, first, end); break;
       }
     } else {
       switch (A.slot[it.entry]) {
-        case kRuleTet1: persist_item<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
-        case kRuleTet4: persist_item<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
-        case kRulePyr8: persist_item<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, A.table[FEA_PYR5], first, end); break;
+        case kRuleTet1: persist_item_call<FEA_TET4, kRuleTet1, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
+        case kRuleTet4: persist_item_call<FEA_TET4, kRuleTet4, OP, PREC, 1>(persist_smem, A.table[FEA_TET4], first, end); break;
+        case kRulePyr8: persist_item_call<FEA_PYR5, kRulePyr8, OP, PREC, 1>(persist_smem, A.table[FEA_PYR5], first, end); break;
         case kRulePrism6:
-          persist_item<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, A.table[FEA_PRISM6], first, end);
+          persist_item_call<FEA_PRISM6, kRulePrism6, OP, PREC, S2>(persist_smem, A.table[FEA_PRISM6], first, end);
           break;
-        default: persist_item<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, A.table[FEA_HEX8], first, end); break;
+        default: persist_item_call<FEA_HEX8, kRuleHex8, OP, PREC, S2>(persist_smem, A.table[FEA_HEX8], first, end); break;
       }
     }
     sched_record(A.S, item, it.entry, t0);

@@ -179,13 +179,26 @@ __device__ __forceinline__ void cofactors(const float J[3][3], float C[3][3]) {
 __device__ __forceinline__ double widen(float x) { return f32_to_f64_exact(x); }
 __device__ __forceinline__ double widen(double x) { return x; }
 
+// FP64 add into global memory that returns nothing: a reduction carried out
+// in L2 on a global-space address (red.global.add.f64), so the warp never
+// waits for it.  atomicAdd compiles to that only where the compiler can tell
+// the pointer is global; in the persistent kernels, whose pointers come from
+// a parameter table indexed at run time, it became a generic-address atomic
+// whose result every warp waited for (ncu: no reduction sectors in L2,
+// long-scoreboard stalls 4.8 per issue against 1.1 in the per-type kernel).
+// A generic-address red behaves the same, hence the explicit conversion.
+__device__ __forceinline__ void red_add(double* p, double v) {
+  const size_t g = __cvta_generic_to_global(p);
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(g), "d"(v) : "memory");
+}
+
 // add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain
 // read-modify-write when no other element of the launch touches the entry
 // (COLOR: the launch holds one color class, Alg. "coloring")
 template <int SC>
 __device__ __forceinline__ void scatter_add(double* p, double v) {
   if constexpr (SC == FEA_SCATTER_ATOMIC)
-    atomicAdd(p, v);
+    red_add(p, v);
   else
     *p += v;
 }

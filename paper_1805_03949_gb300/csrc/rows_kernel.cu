@@ -281,7 +281,7 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
 #pragma unroll
       for (int c2 = 0; c2 < D; ++c2) {
         if (at)
-          atomicAdd(P.A + base + c2, v[c1][c2]);
+          red_add(P.A + base + c2, v[c1][c2]);
         else
           P.A[base + c2] = v[c1][c2];
       }
@@ -293,7 +293,7 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
 #pragma unroll
         for (int c1 = 0; c1 < D; ++c1) {
           if (at)
-            atomicAdd(P.A + base + c1, v[c1][c2]);
+            red_add(P.A + base + c1, v[c1][c2]);
           else
             P.A[base + c1] = v[c1][c2];
         }
@@ -308,7 +308,7 @@ __device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
       for (int c1 = 0; c1 < D; ++c1) {
         const double bv = beta * (OP == FEA_OP_DIFFUSION ? P.src : P.f[c1]);
         if (T.flags & kTaskAtomicB)
-          atomicAdd(P.b + D * gi + c1, bv);
+          red_add(P.b + D * gi + c1, bv);
         else
           P.b[D * gi + c1] = bv;
       }

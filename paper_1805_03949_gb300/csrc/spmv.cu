@@ -18,6 +18,7 @@
 // node columns.
 #include <algorithm>
 
+#include "element.cuh"
 #include "fea_internal.cuh"
 
 namespace fea {
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256, 6) k_spmv_rows(const int64_t* __restrict_
       const int64_t gi = glob ? (int64_t)glob[node] : node;
       double* dst = y + D * gi + (row - node * D);
       if (shared && shared[node])
-        atomicAdd(dst, v);
+        red_add(dst, v);
       else
         *dst = v;
     }

@@ -1,10 +1,11 @@
 """GPU parity at the full workload sizes, in the launch configuration the benchmark times.
 
 The oracle cannot assemble 2-4.5 M elements in seconds, so the full-size
-checks are (a) closed-form properties of the whole pattern (nnz, row lengths,
-sortedness, map round trip on sampled elements) and (b) sampled rows: every
-dof row of ~30 seeded nodes (corners, edges, faces, interior) is recomputed by
-the oracle from all elements in index order and compared entry by entry.
+checks are (a) the whole pattern and map against the oracle's (bit-exact),
+with closed-form properties of the pattern (nnz, row lengths, sortedness, map
+round trip on sampled elements), and (b) sampled rows: every dof row of ~30
+seeded nodes (corners, edges, faces, interior) is recomputed by the oracle from
+all elements in index order and compared entry by entry.
 """
 import numpy as np
 import pytest
@@ -80,6 +81,31 @@ def test_hex128_pattern_closed_form(hex128):
             i = conn[e, a]
             for bb in range(8):
                 assert col[rp[3 * i] + 3 * nmap[e, a, bb]] == 3 * conn[e, bb]
+
+
+def test_hex128_pattern_bit_exact(oracle, hex128):
+    """The whole scalar CSR pattern and the element-to-nonzero map of the 128^3
+    workload (513,599,625 nonzeros, 134 M map entries) equal the oracle's."""
+    fea, mesh, s = hex128
+    rp, col, nmap = oracle.pattern(mesh, 3)
+    assert np.array_equal(s.row_ptr.cpu().numpy(), rp)
+    assert np.array_equal(s.node_map.cpu().numpy(), nmap)
+    del nmap
+    assert np.array_equal(s.col_idx.cpu().numpy(), col)
+
+
+def test_hybrid100_pattern_bit_exact(oracle):
+    """The same for the 4.5 M-element hybrid workload (scalar, non-conforming zones)."""
+    fea = engine()
+    mesh = mg.hybrid_cube(100, 3)
+    s = fea.System.from_mesh(mesh, 1, with_cols=True)
+    try:
+        rp, col, nmap = oracle.pattern(mesh, 1)
+        assert np.array_equal(s.row_ptr.cpu().numpy(), rp)
+        assert np.array_equal(s.col_idx.cpu().numpy(), col)
+        assert np.array_equal(s.node_map.cpu().numpy(), nmap)
+    finally:
+        s.close()
 
 
 @pytest.mark.parametrize("scatter", [3, 0, 1, 2, 4])
