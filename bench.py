@@ -199,13 +199,13 @@ def algorithmic_flops_hex_elasticity(n_elems, n_nodes, nnz, nq=8, nn=8):
     contributions per element into the (nnz + 9 n_nodes) / 2 entries of the
     upper blocks; b: 8 x 3 contributions per element into 3 n_nodes entries.
     FP32 (per point): scaled gradients 8 x 9 FMA + 24 mul, scale 3; per (a <= b)
-    block and point: 3 FMA (dot) + 18 FMA + 3 add; per (a, point) 6 mul; RHS 3 FMA
-    per (a, point).
+    block the moment g_a g_b^T, 9 FMA; RHS 3 FMA per (a, point); once per block
+    lam M + mu M^T + mu tr(M) I, 33.
     """
     geometry = 72 + nq * (2 * 27 + (9 + 2 * 9) + (1 + 2 * 2) + 2)
     blocks = nn * (nn + 1) // 2
     accumulate = (blocks * 9 * n_elems - (nnz + 9 * n_nodes) // 2) + (3 * nn * n_elems - 3 * n_nodes)
-    fp32 = nq * ((2 * 72 + 24 + 3) + blocks * (2 * 3 + 2 * 18 + 3) + nn * 6 + nn * 2 * 3)
+    fp32 = nq * ((2 * 72 + 24 + 3) + blocks * 2 * 9 + nn * 2 * 3) + blocks * 33
     return {"fp64": n_elems * geometry + accumulate, "fp64_geometry": n_elems * geometry,
             "fp64_accumulate": accumulate, "fp32": n_elems * fp32}
 
@@ -238,13 +238,17 @@ def element_flops(etype, op, nq, k_varies=False):
       are constant, taken once with s = 1 / det J from its geometry.
     prod: diffusion, per point k_q g_a (3 mul per node) and, per (a <= b)
       pair, 3 FMA accumulating k_q g_a . g_b into A_ab, plus k_q = k0 + k2 x_q^2
-      (mul + FMA) where k varies; elasticity, per point and (a <= b) block 3 FMA
-      (mu g_a . g_b) + 18 FMA (lam g_a g_b^T + mu g_b g_a^T into A_ab) + 3 adds
-      (the diagonal), and 6 mul per node (lam g_a, mu g_a).  An affine tet, whose
-      gradients are constant, takes its products once: the weight sum W =
-      sum_q w_q det J k_q (1 FMA per point, and k_q), then per pair a dot
-      product (3 FMA) times W (1 mul) for diffusion, per element lam W and mu
-      W (2 mul) and the elasticity block as above.
+      (mul + FMA) where k varies; elasticity, per point and (a <= b) block the
+      moment M_ab += g_a g_b^T (9 FMA), and once per block lam M + mu M^T +
+      mu tr(M) I (2 adds and 1 mul for the trace, 9 x (mul + FMA), 3 adds).
+      An affine tet, whose gradients are constant, takes its products once:
+      the weight sum W = sum_q w_q det J k_q (1 FMA per point, and k_q), then
+      per pair a dot product (3 FMA) times W (1 mul) for diffusion; for
+      elasticity lam W and mu W (2 mul) and per block M (9 FMA) and the
+      combination (33).  J2 (op 2): per point and block three moment sums
+      weighted by lam', mu' and beta (27 FMA), per node and point lam' g_a,
+      mu' g_a (6 mul), h_a = n g_a (9 FMA), beta h_a (3 mul) and the internal
+      force sigma g_a (9 FMA), and per block their combination (23 adds).
     rhs: w det J f_c N_a, 1 FMA per node, component and point.
     """
     nn = NODES_PER_TYPE[etype]
@@ -262,10 +266,18 @@ def element_flops(etype, op, nq, k_varies=False):
     kq = 3 if k_varies else 0
     if op == OP_DIFFUSION:
         prod = 7 * pairs + nq * (2 + kq) if affine else nq * (kq + 3 * nn + 6 * pairs)
+    elif op == OP_J2:
+        # three weighted moment sums per (a <= b) block and point (27 FMA); per
+        # node and point lam' g_a, mu' g_a (6 mul), h_a = n g_a (9 FMA), beta
+        # h_a (3 mul) and the internal force sigma g_a (9 FMA); once per block
+        # the combination (23 adds)
+        prod = nq * (54 * pairs + 45 * nn) + 23 * pairs
     else:
-        per = 45 * pairs + 6 * nn
-        prod = per + 2 + nq * (2 + kq) if affine else nq * per
-    rhs = nq * 2 * nn * d
+        # M_ab = sum_q g_a g_b^T (9 FMA per block and point), then once per
+        # block lam M + mu M^T + mu tr(M) I (33); an affine tet forms M once,
+        # with lam W and mu W (2 mul) and W = sum_q w_q det J (1 FMA per point)
+        prod = 51 * pairs + 2 + 2 * nq if affine else nq * 18 * pairs + 33 * pairs
+    rhs = 0 if op == OP_J2 else nq * 2 * nn * d
     return {"geometry": geometry, "coords": coords, "grad": grad, "prod": prod, "rhs": rhs}
 
 
@@ -308,7 +320,6 @@ def assembly_work(type_counts, n_nodes, nnz_node, op, precision, nq_of=None, k_v
     """
     nq_of = nq_of or {0: 4, 1: 8, 2: 6, 3: 8}
     d = 1 if op == OP_DIFFUSION else 3
-    fop = OP_ELASTICITY if op == OP_J2 else op
     f64 = f32 = 0
     parts = {"geometry": 0, "accumulate": 0, "integrate": 0, "j2_update": 0}
     n_elems = sum(type_counts.values())
@@ -318,15 +329,12 @@ def assembly_work(type_counts, n_nodes, nnz_node, op, precision, nq_of=None, k_v
     for t, c in type_counts.items():
         if not c:
             continue
-        w = element_flops(t, fop, nq_of[t], k_varies)
+        w = element_flops(t, op, nq_of[t], k_varies)
         parts["geometry"] += c * (w["geometry"] + w["coords"])
-        integ = w["grad"] + w["prod"] + w["rhs"]
         if op == OP_J2:
             assert t == 3, "the J2 workload is hex8"
-            nn, nq, pairs = 8, nq_of[t], 36
-            integ += nq * (18 * pairs + 18 * nn)     # beta h_a h_b^T per block; h_a = n g_a and sigma g_a per node
             parts["geometry"] += c * 72              # modal transform of the displacements
-        parts["integrate"] += c * integ
+        parts["integrate"] += c * (w["grad"] + w["prod"] + w["rhs"])
     if op == OP_J2:
         j = j2 or {}
         plastic_extra = j2_point_flops(True, 0) - j2_point_flops(False, 0)
@@ -895,13 +903,13 @@ def workload_hybrid(dev, pk, check, steps=5):
         s.close()
 
 
-def workload_j2(dev, pk, check, steps=5):
+def workload_j2(dev, pk, check, steps=5, n=96):
     """Elastoplastic hex8 (J2 / Voce), 96^3, second load step from the committed first step: the
     plain per-type FP64 atomic assembly, FP32-integrate per type, and the persistent schedules."""
     import torch
     from paper_1805_03949_gb300 import fea, meshgen as mg
     amp = json.load(open(os.path.join(ROOT, "tests", "golden", "j2_amplitude.json")))["amplitude"]
-    mesh, U = mg.j2_workload(96, amp)
+    mesh, U = mg.j2_workload(n, amp)
     s = fea.System.from_mesh(mesh, 3, device=dev, with_cols=False)
     try:
         u = torch.tensor(U.reshape(-1), device=dev)
@@ -911,7 +919,6 @@ def workload_j2(dev, pk, check, steps=5):
         s.assemble(fea.make_operator(kind=fea.FEA_OP_J2, precision=0, u=0.5 * u, state_out=st1))
         st2 = torch.empty_like(st1)
         base = dict(kind=fea.FEA_OP_J2, u=u, state_in=st1, state_out=st2)
-        n = 96
         nodes = sample_hex_nodes(n, 4, count=16) if check else None
         rp_h = s.row_ptr.cpu().numpy() if check else None
         snaps = {}
@@ -949,7 +956,7 @@ def workload_j2(dev, pk, check, steps=5):
         loop_work = {"fp64": work[1]["parts"]["geometry"] + work[1]["parts"]["j2_update"], "fp32": 0,
                      "bytes": mesh.n_elems * (8 * 4 + 2 * 8 * 7 * 8 + 8 * 6 * 8) + mesh.n_nodes * (24 + 24)}
         loop_roof = {k: step_roofline(loop_work, v, pk) for k, v in loop.items()}
-        res = {"workload": "J2 / Voce hex8 96^3 jittered, 884,736 elements, second load step "
+        res = {"workload": f"J2 / Voce hex8 {n}^3 jittered, {mesh.n_elems:,} elements, second load step "
                            f"(amplitude {amp:.4e}, {100 * yield_frac:.1f} % of Gauss points yield)",
                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
                "roofline": roof, "j2_work": j2stats,
@@ -1026,7 +1033,7 @@ def other_workloads(args, dev, pk):
                     ("batch", workload_batch)):
         if key in wanted:
             t0 = time.perf_counter()
-            out[key] = fn(dev, pk, check)
+            out[key] = fn(dev, pk, check, n=args.j2_n) if key == "j2" else fn(dev, pk, check)
             out[key]["wall_s"] = time.perf_counter() - t0
             import torch
             torch.cuda.empty_cache()
@@ -1292,6 +1299,7 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--ref-layers", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="time the default launch parameters")
+    ap.add_argument("--j2-n", type=int, default=96, help="cells per edge of the elastoplastic workload (96)")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip every oracle step: the CPU baseline and the error of each result")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),

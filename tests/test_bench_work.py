@@ -187,8 +187,11 @@ def counted_element(O, etype, X, op, tet_rule, k0=1.0, k2=0.0, f=(1.0, 1.0, 1.0)
                     A[a][bb] = Wk * _dot_acc([(G[a][i], G[bb][i]) for i in range(3)])
         else:
             lw, mw = lam * Wk, mu * Wk
-            _elastic_blocks(A, G, lw, mw, nn)
+            M = {}
+            _moments(M, G, nn)
+            _elastic_blocks(A, M, lw, mw, nn)
     else:
+        M = {}
         for q in range(nq):
             G = grads(q, True)
             if op == bench.OP_DIFFUSION:
@@ -198,7 +201,9 @@ def counted_element(O, etype, X, op, tet_rule, k0=1.0, k2=0.0, f=(1.0, 1.0, 1.0)
                     for bb in range(a, nn):
                         A[a][bb] = _dot_acc([(kG[a][i], G[bb][i]) for i in range(3)], A[a][bb])
             else:
-                _elastic_blocks(A, G, lam, mu, nn)
+                _moments(M, G, nn)
+        if op != bench.OP_DIFFUSION:
+            _elastic_blocks(A, M, lam, mu, nn)
     for q in range(nq):
         N = shapes[q][0]
         wdet = per_point[q][2]
@@ -219,18 +224,26 @@ def counted_element(O, etype, X, op, tet_rule, k0=1.0, k2=0.0, f=(1.0, 1.0, 1.0)
     return An, np.array([x.v for x in b]), dict(COUNT), nq
 
 
-def _elastic_blocks(A, G, lam, mu, nn):
-    """A_ab += lam g_a g_b^T + mu g_b g_a^T + mu (g_a . g_b) I for a <= b."""
-    lg = [[lam * G[a][i] for i in range(3)] for a in range(nn)]
-    mg_ = [[mu * G[a][i] for i in range(3)] for a in range(nn)]
+def _moments(M, G, nn):
+    """M_ab += g_a g_b^T for a <= b (9 FMA per block)."""
     for a in range(nn):
         for bb in range(a, nn):
-            dot = _dot_acc([(mg_[a][i], G[bb][i]) for i in range(3)])
+            m = M.setdefault((a, bb), [[Num(0.0)] * 3 for _ in range(3)])
             for i in range(3):
                 for j in range(3):
-                    r, c = 3 * a + i, 3 * bb + j
-                    A[r][c] = fma(mg_[bb][i], G[a][j], fma(lg[a][i], G[bb][j], A[r][c]))
-                A[3 * a + i][3 * bb + i] = A[3 * a + i][3 * bb + i] + dot
+                    m[i][j] = fma(G[a][i], G[bb][j], m[i][j])
+
+
+def _elastic_blocks(A, M, lam, mu, nn):
+    """A_ab = lam M_ab + mu M_ab^T + mu tr(M_ab) I for a <= b (33 per block)."""
+    for a in range(nn):
+        for bb in range(a, nn):
+            m = M[(a, bb)]
+            mt = mu * (m[0][0] + m[1][1] + m[2][2])
+            for i in range(3):
+                for j in range(3):
+                    A[3 * a + i][3 * bb + j] = fma(lam, m[i][j], mu * m[j][i])
+                A[3 * a + i][3 * bb + i] = A[3 * a + i][3 * bb + i] + mt
 
 
 CASES = [
