@@ -393,9 +393,9 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
 #pragma unroll
         for (int i = 0; i < 3; ++i) sm.X[le][p][i] = v[i];
         __syncwarp();
+        double J[3][3];
+        hex8_jacobian_pairs(sm.X[le], p, J);  // every lane: it exchanges columns with a partner lane
         if (valid) {
-          double J[3][3];
-          hex8_jacobian(sm.X[le], p, J);
           double xq = 0.0;
           if constexpr (OP == FEA_OP_DIFFUSION) {
             const double g = 0.57735026918962576451;

@@ -130,6 +130,35 @@ __device__ __forceinline__ void hex8_jacobian(const double (*c)[3], int q, doubl
   }
 }
 
+// The same J' for the lane's own point, with the work shared by the 8 lanes of
+// an element (lane p of an aligned group of 8 holds point p; every lane of the
+// warp must call it).  Column 0 depends only on (y, z) and column 1 only on
+// (x, z), so each takes 4 distinct values over the 8 points: lanes whose bits 0
+// and 1 agree form column 0, the others column 1, and each lane takes the
+// column it lacks from the partner with the same coordinates (lane p ^ 2 for
+// column 1, p ^ 1 for column 0).  Column 2 every lane forms itself.  18 FMAs
+// per point instead of 27, in the same order as hex8_jacobian (the same J).
+__device__ __forceinline__ void hex8_jacobian_pairs(const double (*c)[3], int q, double J[3][3]) {
+  constexpr double g = 0.57735026918962576451;
+  constexpr double g2 = g * g;
+  const double x = (q & 1) ? g : -g, y = (q & 2) ? g : -g, z = (q & 4) ? g : -g;
+  const double xy = ((q ^ (q >> 1)) & 1) ? -g2 : g2;
+  const double xz = ((q ^ (q >> 2)) & 1) ? -g2 : g2;
+  const double yz = (((q >> 1) ^ (q >> 2)) & 1) ? -g2 : g2;
+  const bool first = ((q ^ (q >> 1)) & 1) == 0;  // this lane forms column 0
+  const double s = first ? y : x, st = first ? yz : xz;
+  const int partner = (int)(threadIdx.x & 31) ^ (first ? 2 : 1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double ca = first ? c[1][i] : c[2][i], cc = first ? c[5][i] : c[6][i];
+    const double own = fma(c[7][i], st, fma(cc, z, fma(c[3][i], s, ca)));
+    const double other = __shfl_sync(0xffffffffu, own, partner);
+    J[i][0] = first ? own : other;
+    J[i][1] = first ? other : own;
+    J[i][2] = fma(c[7][i], xy, fma(c[6][i], y, fma(c[5][i], x, c[4][i])));
+  }
+}
+
 // FP64 -> FP32, rounded to nearest even, with integer instructions (IEEE 754
 // binary64 to binary32): the 52-bit significand keeps its top 23 bits and
 // rounds up when the 29 dropped bits exceed half an ulp, or equal it with an

@@ -189,9 +189,9 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
 #pragma unroll
       for (int i = 0; i < 3; ++i) sX[le][p][i] = v[i];
       __syncwarp();
+      double J[3][3];
+      hex8_jacobian_pairs(sX[le], q, J);  // every lane: it exchanges columns with a partner lane
       if (valid) {
-        double J[3][3];
-        hex8_jacobian(sX[le], q, J);
         double xq = 0.0;
         if (P.diffusion) {
           // x(xi_q) = x_0 + (1/8) sum_k c_k prod_{s in k} xi_s

@@ -316,16 +316,16 @@ __device__ __forceinline__ void j2_tile_body(typename J2Cfg<TYPE, SLOT, PREC, SP
         if constexpr (kModalU) sm.U[le][p][i] = vu[i];
       }
       __syncwarp();
+      // every lane forms its Jacobians (the lanes of an element exchange
+      // columns); the valid ones use them
+      double J[3][3], Ju[3][3];
+      hex8_jacobian_pairs(sm.X[le], p, J);
+      if constexpr (kModalU) hex8_jacobian_pairs(sm.U[le], p, Ju);
       if (valid) {
-        double J[3][3];
-        hex8_jacobian(sm.X[le], p, J);
-        if constexpr (kModalU) {
-          double Ju[3][3];
-          hex8_jacobian(sm.U[le], p, Ju);
+        if constexpr (kModalU)
           j2_point<Cfg, true>(sm, rr, P, le, p, et, J, 8.0, Ju);
-        } else {
+        else
           j2_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
-        }
       }
     }
   } else {

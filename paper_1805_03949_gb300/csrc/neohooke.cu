@@ -222,16 +222,16 @@ __device__ __forceinline__ void nh_tile_body(typename NHCfg<TYPE, SLOT, PREC, SP
         if constexpr (kModalU) sm.U[le][p][i] = vu[i];
       }
       __syncwarp();
+      // every lane forms its Jacobians (the lanes of an element exchange
+      // columns); the valid ones use them
+      double J[3][3], Ju[3][3];
+      hex8_jacobian_pairs(sm.X[le], p, J);
+      if constexpr (kModalU) hex8_jacobian_pairs(sm.U[le], p, Ju);
       if (valid) {
-        double J[3][3];
-        hex8_jacobian(sm.X[le], p, J);
-        if constexpr (kModalU) {
-          double Ju[3][3];
-          hex8_jacobian(sm.U[le], p, Ju);
+        if constexpr (kModalU)
           nh_point<Cfg, true>(sm, rr, P, le, p, et, J, 8.0, Ju);
-        } else {
+        else
           nh_point<Cfg>(sm, rr, P, le, p, et, J, 8.0);
-        }
       }
     }
   } else {

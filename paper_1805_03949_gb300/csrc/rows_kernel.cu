@@ -118,9 +118,9 @@ __device__ __forceinline__ void hex_record(const RowsArgs& P, bool valid, const 
   for (int k = 0; k < 8; ++k)
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[k][i] = __shfl_sync(0xffffffffu, v[i], base | k);
-  if (!valid) return;
   double J[3][3];
-  hex8_jacobian(c, p, J);
+  hex8_jacobian_pairs(c, p, J);  // every lane (it exchanges columns)
+  if (!valid) return;
   double C[3][3];
   cofactors(J, C);
   const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
