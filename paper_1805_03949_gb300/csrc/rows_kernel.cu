@@ -180,139 +180,169 @@ __device__ __forceinline__ float tile_param<float>(double, float f) {
   return f;
 }
 
-// The entry-block tasks of one block, by threads tid, tid + nthreads, ...
-// (records staged in shared memory when STAGE, in layout L, else read from
-// `rec`, whose records have L's offsets and kRecStride values each).
-template <int OP, int PREC, bool HEX, bool STAGE, class L = RecCopied>
-__device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
-                                          const typename std::conditional<PREC == FEA_FP64, double, float>::type* s_recs,
-                                          const int64_t* s_rs, const RowTask* s_tasks, const uint16_t* s_contrib,
-                                          const int32_t* s_hid, const int32_t* gnode, int tid, int nthreads) {
+// One entry-block task t of a block: its element contributions summed in
+// registers, the entry block stored (or added, at block boundaries) to row i
+// and, transposed, to row j; the right-hand side of node i with the
+// diagonal task.  Records staged in shared memory when STAGE, in layout L,
+// else read from `rec`, whose records have L's offsets and kRecStride values
+// each.
+template <int OP, int PREC, bool HEX, bool STAGE, class L>
+__device__ __forceinline__ void run_task(const RowsArgs& P, const RowBlock& H,
+                                         const typename std::conditional<PREC == FEA_FP64, double, float>::type* s_recs,
+                                         const int64_t* s_rs, const RowTask* s_tasks, const uint16_t* s_contrib,
+                                         const int32_t* s_hid, const int32_t* gnode, int t) {
   using R = typename std::conditional<PREC == FEA_FP64, double, float>::type;
   constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
   const R* rec = reinterpret_cast<const R*>(P.rec);
   const R lam = tile_param<R>(P.lam, P.lamf), mu = tile_param<R>(P.mu, P.muf);
-  for (int t = tid; t < H.n_tasks; t += nthreads) {
-    const RowTask T = s_tasks[t];
-    const bool diag = T.flags & kTaskDiag;
-    Acc<PREC> acc[D][D];
-    Acc<PREC> bsum;   // sum over the contributions of w det J N_a (b_i = f times it)
+  const RowTask T = s_tasks[t];
+  const bool diag = T.flags & kTaskDiag;
+  Acc<PREC> acc[D][D];
+  Acc<PREC> bsum;   // sum over the contributions of w det J N_a (b_i = f times it)
 #pragma unroll 1
-    for (int c = 0; c < T.nc; ++c) {
-      const int code = s_contrib[T.coff + c];
-      const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
-      const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
-      const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
-      const R* re = STAGE ? s_recs + (size_t)h * L::stride : rec + (int64_t)s_hid[h] * kRecStride;
-      const R* ga = re + 3 * a;
-      const R* gb = re + 3 * bn;
-      R K[D][D];
-      if constexpr (OP == FEA_OP_DIFFUSION) {
-        R s = R(0);
+  for (int c = 0; c < T.nc; ++c) {
+    const int code = s_contrib[T.coff + c];
+    const int h = code >> 6, a = (code >> 3) & 7, bn = code & 7;
+    const int type = HEX ? (int)FEA_HEX8 : (int)__ldg(P.helem_type + H.helem_off + h);
+    const int nq = HEX ? 8 : (type == FEA_TET4 ? P.tet_nq : type == FEA_PRISM6 ? 6 : 8);
+    const R* re = STAGE ? s_recs + (size_t)h * L::stride : rec + (int64_t)s_hid[h] * kRecStride;
+    const R* ga = re + 3 * a;
+    const R* gb = re + 3 * bn;
+    R K[D][D];
+    if constexpr (OP == FEA_OP_DIFFUSION) {
+      R s = R(0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (!HEX && q >= nq) break;
-          const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
-                  x2 = ld_rec<STAGE>(ga + L::q * q + 2);
-          const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
-                  y2 = ld_rec<STAGE>(gb + L::q * q + 2);
-          s += ld_rec<STAGE>(re + L::k + q) * (x0 * y0 + x1 * y1 + x2 * y2);
-        }
-        K[0][0] = s;
-      } else {
-        R M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (!HEX && q >= nq) break;
-          const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
-                  x2 = ld_rec<STAGE>(ga + L::q * q + 2);
-          const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
-                  y2 = ld_rec<STAGE>(gb + L::q * q + 2);
-          M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
-          M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
-          M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
-        }
-        const R tr = mu * (M[0][0] + M[1][1] + M[2][2]);
-#pragma unroll
-        for (int c1 = 0; c1 < 3; ++c1)
-#pragma unroll
-          for (int c2 = 0; c2 < 3; ++c2) K[c1][c2] = lam * M[c1][c2] + mu * M[c2][c1] + (c1 == c2 ? tr : R(0));
+      for (int q = 0; q < 8; ++q) {
+        if (!HEX && q >= nq) break;
+        const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
+                x2 = ld_rec<STAGE>(ga + L::q * q + 2);
+        const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
+                y2 = ld_rec<STAGE>(gb + L::q * q + 2);
+        s += ld_rec<STAGE>(re + L::k + q) * (x0 * y0 + x1 * y1 + x2 * y2);
       }
-      if (c == 0) {
+      K[0][0] = s;
+    } else {
+      R M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-        for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-          for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].set(K[c1][c2]);
-      } else {
-#pragma unroll
-        for (int c1 = 0; c1 < D; ++c1)
-#pragma unroll
-          for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].add(K[c1][c2]);
+      for (int q = 0; q < 8; ++q) {
+        if (!HEX && q >= nq) break;
+        const R x0 = ld_rec<STAGE>(ga + L::q * q), x1 = ld_rec<STAGE>(ga + L::q * q + 1),
+                x2 = ld_rec<STAGE>(ga + L::q * q + 2);
+        const R y0 = ld_rec<STAGE>(gb + L::q * q), y1 = ld_rec<STAGE>(gb + L::q * q + 1),
+                y2 = ld_rec<STAGE>(gb + L::q * q + 2);
+        M[0][0] += x0 * y0; M[0][1] += x0 * y1; M[0][2] += x0 * y2;
+        M[1][0] += x1 * y0; M[1][1] += x1 * y1; M[1][2] += x1 * y2;
+        M[2][0] += x2 * y0; M[2][1] += x2 * y1; M[2][2] += x2 * y2;
       }
-      if (diag) {
-        const int slot = HEX ? (int)kRuleHex8 : rule_slot_of(type, P.tet_nq);
-        R rb = R(0);
-        for (int q = 0; q < nq; ++q) {
-          R Nqa;
-          if constexpr (PREC == FEA_FP64)
-            Nqa = P.Ntab64[slot][q][a];
-          else
-            Nqa = P.Ntab[slot][q][a];
-          rb += ld_rec<STAGE>(re + L::w + q) * Nqa;
-        }
-        if (c == 0)
-          bsum.set(rb);
-        else
-          bsum.add(rb);
-      }
+      const R tr = mu * (M[0][0] + M[1][1] + M[2][2]);
+#pragma unroll
+      for (int c1 = 0; c1 < 3; ++c1)
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) K[c1][c2] = lam * M[c1][c2] + mu * M[c2][c1] + (c1 == c2 ? tr : R(0));
     }
-    // the entry block, rounded once, to row i and transposed to row j
-    double v[D][D];
+    if (c == 0) {
 #pragma unroll
-    for (int c1 = 0; c1 < D; ++c1)
+      for (int c1 = 0; c1 < D; ++c1)
 #pragma unroll
-      for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
-    // complete entries are stored; block-boundary entries (block-task plan)
-    // are added to A with FP64 atomics
-    const bool at = T.flags & kTaskAtomicA;
+        for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].set(K[c1][c2]);
+    } else {
 #pragma unroll
-    for (int c1 = 0; c1 < D; ++c1) {
-      const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
+      for (int c1 = 0; c1 < D; ++c1)
 #pragma unroll
-      for (int c2 = 0; c2 < D; ++c2) {
-        if (at)
-          red_add(P.A + base + c2, v[c1][c2]);
-        else
-          P.A[base + c2] = v[c1][c2];
-      }
-    }
-    if (T.flags & kTaskTranspose) {
-#pragma unroll
-      for (int c2 = 0; c2 < D; ++c2) {
-        const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
-#pragma unroll
-        for (int c1 = 0; c1 < D; ++c1) {
-          if (at)
-            red_add(P.A + base + c1, v[c1][c2]);
-          else
-            P.A[base + c1] = v[c1][c2];
-        }
-      }
+        for (int c2 = 0; c2 < D; ++c2) acc[c1][c2].add(K[c1][c2]);
     }
     if (diag) {
-      // the source is constant over the mesh: b_i = f (sum of the element
-      // integrals of N_a), one FP64 product per component
-      const int64_t gi = gnode[T.li];
-      const double beta = bsum.value();
+      const int slot = HEX ? (int)kRuleHex8 : rule_slot_of(type, P.tet_nq);
+      R rb = R(0);
+      for (int q = 0; q < nq; ++q) {
+        R Nqa;
+        if constexpr (PREC == FEA_FP64)
+          Nqa = P.Ntab64[slot][q][a];
+        else
+          Nqa = P.Ntab[slot][q][a];
+        rb += ld_rec<STAGE>(re + L::w + q) * Nqa;
+      }
+      if (c == 0)
+        bsum.set(rb);
+      else
+        bsum.add(rb);
+    }
+  }
+  // the entry block, rounded once, to row i and transposed to row j
+  double v[D][D];
+#pragma unroll
+  for (int c1 = 0; c1 < D; ++c1)
+#pragma unroll
+    for (int c2 = 0; c2 < D; ++c2) v[c1][c2] = acc[c1][c2].value();
+  // complete entries are stored; block-boundary entries (block-task plan)
+  // are added to A with FP64 atomics
+  const bool at = T.flags & kTaskAtomicA;
+#pragma unroll
+  for (int c1 = 0; c1 < D; ++c1) {
+    const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
+#pragma unroll
+    for (int c2 = 0; c2 < D; ++c2) {
+      if (at)
+        red_add(P.A + base + c2, v[c1][c2]);
+      else
+        P.A[base + c2] = v[c1][c2];
+    }
+  }
+  if (T.flags & kTaskTranspose) {
+#pragma unroll
+    for (int c2 = 0; c2 < D; ++c2) {
+      const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
 #pragma unroll
       for (int c1 = 0; c1 < D; ++c1) {
-        const double bv = beta * (OP == FEA_OP_DIFFUSION ? P.src : P.f[c1]);
-        if (T.flags & kTaskAtomicB)
-          red_add(P.b + D * gi + c1, bv);
+        if (at)
+          red_add(P.A + base + c1, v[c1][c2]);
         else
-          P.b[D * gi + c1] = bv;
+          P.A[base + c1] = v[c1][c2];
       }
     }
+  }
+  if (diag) {
+    // the source is constant over the mesh: b_i = f (sum of the element
+    // integrals of N_a), one FP64 product per component
+    const int64_t gi = gnode[T.li];
+    const double beta = bsum.value();
+#pragma unroll
+    for (int c1 = 0; c1 < D; ++c1) {
+      const double bv = beta * (OP == FEA_OP_DIFFUSION ? P.src : P.f[c1]);
+      if (T.flags & kTaskAtomicB)
+        red_add(P.b + D * gi + c1, bv);
+      else
+        P.b[D * gi + c1] = bv;
+    }
+  }
+}
+
+// the first of the next 32 tasks of the block, for the whole warp (every
+// lane calls it)
+__device__ __forceinline__ int grab_tasks(int* s_next) {
+  int t0 = 0;
+  if ((threadIdx.x & 31) == 0) t0 = atomicAdd(s_next, 32);
+  return __shfl_sync(0xffffffffu, t0, 0);
+}
+
+// The entry-block tasks of one block, 32 consecutive tasks per warp.  The
+// tasks are sorted by contribution count, largest first.  With s_next (a
+// shared counter, zero at the start of the block) the warps take batches as
+// they finish, so the largest go first and no warp is left holding all of
+// them; without it the warp of threads tid..tid+31 takes batches tid,
+// tid + nthreads, ... (tid a multiple of 32 at the warp's first lane,
+// nthreads a multiple of 32).  Which warp runs a task does not change what it
+// computes.
+template <int OP, int PREC, bool HEX, bool STAGE, class L = RecCopied>
+__device__ __forceinline__ void run_tasks(const RowsArgs& P, const RowBlock& H,
+                                          const typename std::conditional<PREC == FEA_FP64, double, float>::type* s_recs,
+                                          const int64_t* s_rs, const RowTask* s_tasks, const uint16_t* s_contrib,
+                                          const int32_t* s_hid, const int32_t* gnode, int tid, int nthreads,
+                                          int* s_next = nullptr) {
+  for (int t0 = s_next ? grab_tasks(s_next) : (tid & ~31); t0 < H.n_tasks;
+       t0 = s_next ? grab_tasks(s_next) : t0 + nthreads) {
+    const int t = t0 + (tid & 31);
+    if (t < H.n_tasks) run_task<OP, PREC, HEX, STAGE, L>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, gnode, t);
   }
 }
 
@@ -333,6 +363,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem_raw + P.L.bar);
   const R* rec = reinterpret_cast<const R*>(P.rec);
   if (threadIdx.x == 0) mbar_init(s_bar);
+  __shared__ int s_next;  // the block's next batch of tasks
   __syncthreads();
   uint32_t parity = 0;
   for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, parity ^= 1u) {
@@ -340,6 +371,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
     if (threadIdx.x < 32) {
       const uint32_t rec_bytes = (STAGE && !GEO) ? (uint32_t)(4 * kRecStride) * H.n_helem : 0u;
       if (threadIdx.x == 0) {
+        s_next = 0;  // read after the barrier below
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order earlier reads of the buffers
         mbar_expect_tx(s_bar, H.task_bytes + H.contrib_bytes + H.helem_bytes + rec_bytes);
         if (H.task_bytes) bulk_copy_g2s(s_tasks, P.tasks + H.task_off, H.task_bytes, s_bar);
@@ -376,7 +408,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
       mbar_wait_bounded(s_bar, parity);
       return;
     }
-    run_tasks<OP, PREC, HEX, STAGE>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, lnodes, threadIdx.x, blockDim.x);
+    run_tasks<OP, PREC, HEX, STAGE>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, lnodes, threadIdx.x, blockDim.x,
+                                    &s_next);
     __syncthreads();
   }
 }
@@ -384,14 +417,17 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 // ---------------------------------------------------------------------------
 // Block-task plans of hex meshes in FP32-integrate, pipelined: one persistent
 // CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
-// shared-memory stages.  Warps 0-5 (producers) fill stage i & 1 for block i:
-// the task lists by TMA bulk copy; the row starts and node ids of the block's
-// nodes; and the FP64-geometry records of the block's elements, whose corner
-// coordinates come from a copy of the block's node coordinates in shared
-// memory (one gather per node, not per corner).  Warps 6-15 (consumers) run
-// the tasks of block i - 1 meanwhile.  The stages are handed over by
-// mbarriers: full[s] (1 arrival with the copy bytes + 192 producer arrivals)
-// and empty[s] (320 consumer arrivals).  The producers also meet at a named
+// shared-memory stages.  Warps 0..PW-1 (producers) fill stage i & 1 for
+// block i: the task lists by TMA bulk copy; the row starts and node ids of
+// the block's nodes; and the FP64-geometry records of the block's elements,
+// whose corner coordinates come from a copy of the block's node coordinates
+// in shared memory (one gather per node, not per corner).  Warps PW..15
+// (consumers) run the tasks of block i - 1 meanwhile, in batches of 32 taken
+// from a per-stage counter: the first consumer warp would otherwise hold the
+// largest tasks of every round, and the stage is released only when its
+// slowest consumer is done.  The stages are handed over by mbarriers: full[s]
+// (1 arrival with the copy bytes + 32 PW producer arrivals) and empty[s]
+// (32 (16 - PW) consumer arrivals).  The producers also meet at a named
 // barrier (id 1) twice per block, around their shared coordinate copy; the
 // decision to stop after a timeout is taken there by all of them at once, so
 // none is left waiting.  Every wait is bounded; a timeout latches
@@ -430,6 +466,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   uint64_t* empty = full + 2;
   double* s_x = reinterpret_cast<double*>(pipe_raw + 2 * stage_bytes + 32);  // producers' node coordinates
   __shared__ int s_issued[2];
+  __shared__ int s_next[2];  // each stage's next batch of tasks
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
     mbar_init_count(&full[0], kPipeProducers + 1);
@@ -463,6 +500,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       // also finished reading the coordinate copy of the previous block
       if (producers_any<kPipeProducers>(*((volatile int*)&s_fail) != 0)) break;
       if (threadIdx.x == 0) {
+        s_next[s] = 0;  // published to the consumers by the arrival on full[s]
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
         mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
         if (H.task_bytes) bulk_copy_g2s(s_tasks, P.tasks + H.task_off, H.task_bytes, &full[s]);
@@ -507,7 +545,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         break;
       }
       run_tasks<OP, FEA_FP32_INTEGRATE, true, true, RecPipe>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, s_gi,
-                                                             (int)threadIdx.x - kPipeProducers, kPipeConsumers);
+                                                             (int)threadIdx.x - kPipeProducers, kPipeConsumers,
+                                                             &s_next[s]);
       mbar_arrive(&empty[s]);
     }
   }
