@@ -304,6 +304,8 @@ int fea_build_csr_pattern(fea_mesh* mesh, int ndof, int64_t* row_ptr_d, int32_t*
  * OVERWRITES A_vals_d (float64 [nnz]) and b_d (float64 [n_nodes*ndof]) with
  * sum_e P_e^T A^e P_e and sum_e P_e^T b^e, using the pattern and map written
  * by fea_build_csr_pattern for ndof = 1 (diffusion) or 3 (elasticity).
+ * A_vals_d must be 16-byte aligned (cudaMalloc and PyTorch allocations are)
+ * and b_d 8-byte aligned, else -1 (FEA_ERR_ARG) before any work.
  * Stream-ordered; an inverted element is latched in the mesh status and
  * reported by fea_check (the values are then unspecified). */
 int fea_assemble(const fea_operator* op, fea_mesh* mesh, const int64_t* row_ptr_d,
@@ -584,6 +586,16 @@ int fea_check(fea_mesh* mesh, void* stream);
  * the rate is taken over the CUDA-event time of the timed launch on `stream`.
  * Allocates a small scratch buffer.  Synchronous. */
 int fea_peak_probe(int kind, int64_t iters, double* flops, void* stream);
+
+/* The precision conversions of the FP32-integrate kernels, elementwise on n
+ * device values: dir 0 widens FP32 `in` to FP64 `out` exactly (every FP32
+ * contribution enters the FP64 accumulation this way); dir 1 rounds FP64 `in`
+ * to FP32 `out` to nearest, ties to even (FP64 geometry to FP32 records).  Both
+ * use integer instructions instead of the FP64 pipe, and both must equal the
+ * IEEE 754 conversions bit for bit (NaN: a NaN).  The paper has no counterpart:
+ * it exists so that the conversions can be checked.  Asynchronous on
+ * `stream`; n = 0 does nothing.  -1 for a bad dir, n < 0 or a null buffer. */
+int fea_convert(int dir, const void* in_d, void* out_d, int64_t n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,13 @@ const RefRule& host_rule(int slot);
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double f32_to_f64_exact(float x) {
   const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7fffffffu;
+  if (mag - 0x00800000u < 0x7f000000u) {
+    // a normal number: the exponent field moves 3 bits down and its bias
+    // grows by 1023 - 127 = 896; the 23 fraction bits split 20 | 3 across
+    // the two words
+    return __hiloint2double((int)(((mag >> 3) + (896u << 20)) | (u & 0x80000000u)), (int)(u << 29));
+  }
   const uint32_t sign = u & 0x80000000u;
   int e = (int)((u >> 23) & 0xffu);
   uint32_t m = u & 0x7fffffu;
@@ -219,6 +226,12 @@ __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ void red_add(double* p, double v) {
   const size_t g = __cvta_generic_to_global(p);
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(g), "d"(v) : "memory");
+}
+
+// a request to bring the line holding p into L2; nothing is returned and
+// nothing waits for it
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
 }
 
 // add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain

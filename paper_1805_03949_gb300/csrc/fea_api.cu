@@ -261,6 +261,9 @@ int fea_build_csr_pattern(fea_mesh* m, int ndof, int64_t* row_ptr, int32_t* col_
 
 int fea_assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const int32_t* node_map,
                  double* A, double* b, void* stream) {
+  // rows of complete entry blocks are written with 16-byte stores
+  if (((uintptr_t)A & 15u) != 0 || ((uintptr_t)b & 7u) != 0)
+    return fail(FEA_ERR_ARG, "fea_assemble: A_vals_d must be 16-byte aligned and b_d 8-byte aligned");
   return fea::assemble(op, m, row_ptr, node_map, A, b, (cudaStream_t)stream);
 }
 

@@ -8,11 +8,25 @@
 // values stay normal and finite whatever the length.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
+#include "element.cuh"
 #include "fea_internal.cuh"
 
 namespace fea {
+
+// the kernels' own precision conversions, elementwise (dir 0: FP32 -> FP64
+// exact widening; dir 1: FP64 -> FP32 rounded to nearest even), by integer
+// instructions as in the assembly kernels
+__global__ void k_convert(int dir, const void* in, void* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (dir == 0)
+      static_cast<double*>(out)[i] = f32_to_f64_exact(static_cast<const float*>(in)[i]);
+    else
+      static_cast<float*>(out)[i] = f64_to_f32_rn(static_cast<const double*>(in)[i]);
+  }
+}
 
 constexpr int kProbeChains = 8;
 constexpr int kProbeThreads = 256;
@@ -70,6 +84,17 @@ static int run_probe(int64_t iters, double* flops, cudaStream_t s) {
 }
 
 }  // namespace fea
+
+extern "C" int fea_convert(int dir, const void* in, void* out, int64_t n, void* stream) {
+  using namespace fea;
+  if ((dir != 0 && dir != 1) || n < 0 || (n > 0 && (!in || !out)))
+    return fail(FEA_ERR_ARG, "fea_convert: dir 0 or 1, n >= 0, buffers not null");
+  if (n == 0) return FEA_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_convert<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(dir, in, out, n);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
 
 extern "C" int fea_peak_probe(int kind, int64_t iters, double* flops, void* stream) {
   using namespace fea;

@@ -331,15 +331,17 @@ int upload_plan(std::vector<HostBlock>& blocks, int ndof, int block_nodes, int h
 
 static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-// Shared memory of one block: its owned row starts, and the task, contribution
-// and halo-element lists (bulk-copied, 16-byte padded); the element data
-// itself is read from the geometry records through L1.
-RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats) {
+// Shared memory of one block: its owned row starts and node ids (unless
+// node_data is false: the pipelined kernel keeps them in its node buffers),
+// and the task, contribution and halo-element lists (bulk-copied, 16-byte
+// padded); the element records when staged.
+RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats, bool node_data) {
   RowsLayout L;
   uint32_t o = 0;
+  const uint32_t owned = node_data ? (uint32_t)P.max_owned : 0u;
   L.recs = o;                  o += stage ? (uint32_t)(4 * rec_floats * P.max_helem) : 0u;
-  L.rs = align_up(o, 16);      o = L.rs + 8u * P.ndof * P.max_owned;
-  L.gi = o;                    o += 4u * P.max_owned;
+  L.rs = align_up(o, 16);      o = L.rs + 8u * P.ndof * owned;
+  L.gi = o;                    o += 4u * owned;
   L.tasks = align_up(o, 16);   o = L.tasks + (uint32_t)(sizeof(RowTask) * P.max_tasks);
   L.contrib = align_up(o, 16); o = L.contrib + (uint32_t)(2 * P.max_contrib);
   L.hid = align_up(o, 16);     o = L.hid + (uint32_t)(4 * P.max_helem_padded);

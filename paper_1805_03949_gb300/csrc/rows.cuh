@@ -110,7 +110,7 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
 int ensure_rows_plan(fea_mesh* m, int ndof, int precision, cudaStream_t s, RowsPlan** out);
 void drop_rows_plans(fea_mesh* m);
 void free_rows_plan(RowsPlan* P);
-RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats = kRowsRecSmem);
+RowsLayout rows_layout(const RowsPlan& P, bool stage, int rec_floats = kRowsRecSmem, bool node_data = true);
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
                   cudaStream_t s, int* launched);
 // the block-task plan of a mesh, built on first use

@@ -180,6 +180,19 @@ __device__ __forceinline__ float tile_param<float>(double, float f) {
   return f;
 }
 
+// three consecutive values of A at p = A + e: one 16-byte and one 8-byte
+// store (A is 16-byte aligned, so p is when e is even) instead of three, and
+// fewer sectors to request from L2
+__device__ __forceinline__ void store3(double* p, int64_t e, double a0, double a1, double a2) {
+  if ((e & 1) == 0) {
+    *reinterpret_cast<double2*>(p) = make_double2(a0, a1);
+    p[2] = a2;
+  } else {
+    p[0] = a0;
+    *reinterpret_cast<double2*>(p + 1) = make_double2(a1, a2);
+  }
+}
+
 // One entry-block task t of a block: its element contributions summed in
 // registers, the entry block stored (or added, at block boundaries) to row i
 // and, transposed, to row j; the right-hand side of node i with the
@@ -280,24 +293,26 @@ __device__ __forceinline__ void run_task(const RowsArgs& P, const RowBlock& H,
 #pragma unroll
   for (int c1 = 0; c1 < D; ++c1) {
     const int64_t base = s_rs[D * T.li + c1] + (int64_t)D * T.k;
+    if (at) {
 #pragma unroll
-    for (int c2 = 0; c2 < D; ++c2) {
-      if (at)
-        red_add(P.A + base + c2, v[c1][c2]);
-      else
-        P.A[base + c2] = v[c1][c2];
+      for (int c2 = 0; c2 < D; ++c2) red_add(P.A + base + c2, v[c1][c2]);
+    } else if constexpr (D == 3) {
+      store3(P.A + base, base, v[c1][0], v[c1][1], v[c1][2]);
+    } else {
+      P.A[base] = v[0][0];
     }
   }
   if (T.flags & kTaskTranspose) {
 #pragma unroll
     for (int c2 = 0; c2 < D; ++c2) {
       const int64_t base = s_rs[D * T.lj + c2] + (int64_t)D * T.kt;
+      if (at) {
 #pragma unroll
-      for (int c1 = 0; c1 < D; ++c1) {
-        if (at)
-          red_add(P.A + base + c1, v[c1][c2]);
-        else
-          P.A[base + c1] = v[c1][c2];
+        for (int c1 = 0; c1 < D; ++c1) red_add(P.A + base + c1, v[c1][c2]);
+      } else if constexpr (D == 3) {
+        store3(P.A + base, base, v[0][c2], v[1][c2], v[2][c2]);
+      } else {
+        P.A[base] = v[0][0];
       }
     }
   }
@@ -323,6 +338,13 @@ __device__ __forceinline__ int grab_tasks(int* s_next) {
   int t0 = 0;
   if ((threadIdx.x & 31) == 0) t0 = atomicAdd(s_next, 32);
   return __shfl_sync(0xffffffffu, t0, 0);
+}
+
+// the first of the next 4 elements of the block, for the whole warp
+__device__ __forceinline__ int grab_elements(int* s_enext) {
+  int e0 = 0;
+  if ((threadIdx.x & 31) == 0) e0 = atomicAdd(s_enext, 4);
+  return __shfl_sync(0xffffffffu, e0, 0);
 }
 
 // The entry-block tasks of one block, 32 consecutive tasks per warp.  The
@@ -416,145 +438,207 @@ __global__ void __launch_bounds__(256, 2) k_rows_assemble(const __grid_constant_
 
 // ---------------------------------------------------------------------------
 // Block-task plans of hex meshes in FP32-integrate, pipelined: one persistent
-// CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x with two
-// shared-memory stages.  Warps 0..PW-1 (producers) fill stage i & 1 for
-// block i: the task lists by TMA bulk copy; the row starts and node ids of
-// the block's nodes; and the FP64-geometry records of the block's elements,
-// whose corner coordinates come from a copy of the block's node coordinates
-// in shared memory (one gather per node, not per corner).  Warps PW..15
-// (consumers) run the tasks of block i - 1 meanwhile, in batches of 32 taken
-// from a per-stage counter: the first consumer warp would otherwise hold the
-// largest tasks of every round, and the stage is released only when its
-// slowest consumer is done.  The stages are handed over by mbarriers: full[s]
-// (1 arrival with the copy bytes + 32 PW producer arrivals) and empty[s]
-// (32 (16 - PW) consumer arrivals).  The producers also meet at a named
-// barrier (id 1) twice per block, around their shared coordinate copy; the
-// decision to stop after a timeout is taken there by all of them at once, so
-// none is left waiting.  Every wait is bounded; a timeout latches
-// FEA_ERR_TIMEOUT, and the copies in flight are waited for before exit.
-// The split between producer and consumer warps (PW + 16 - PW) is a
+// CTA per SM works through its blocks blk = blockIdx.x + i gridDim.x.  Two
+// shared-memory stages hold a block's task lists and records; three node
+// buffers hold its nodes' row starts, ids and coordinates and its elements'
+// corner lists.
+//  * Warps 0..PW-1 (producers) compute the FP64-geometry records of block i
+//    from node buffer i % 3 into stage i & 1, 4 elements per warp at a time
+//    from a per-stage counter; a warp that finds none left arrives on full[s]
+//    and goes on to block i + 1, so no producer waits for another.
+//  * Warp 0 also leads: once the consumers release stage i & 1 (block
+//    i - 2) it starts the TMA bulk copies of block i's task lists into it and
+//    arrives on ready[i % 3], which lets the producers start; then, before its
+//    own share of block i, it gathers block i + 1's node data into node buffer
+//    (i + 1) % 3 (last read by block i - 2).  The gather is off the chain
+//    from one block's release to the next one's records.
+//  * Warps PW..15 (consumers) run the tasks of the block whose stage is full,
+//    32 at a time from a per-stage counter (the tasks are sorted largest
+//    first; with a fixed share the first consumer warp would hold the largest
+//    of every round, and the stage is released only when its slowest
+//    consumer is done).
+// mbarriers hand the buffers over: ready[b] (32 lead arrivals), full[s] (1
+// arrival with the copy bytes + 32 PW producer arrivals) and empty[s]
+// (32 (16 - PW) consumer arrivals).  Every wait is bounded; a timeout latches
+// FEA_ERR_TIMEOUT and every role leaves its loop at its next look at the
+// shared failure flag (no role waits at a named barrier); the copies in
+// flight are waited for before exit.  The producer/consumer split is a
 // template parameter, chosen per mesh (fea_mesh_set_pipe_split, or the
 // autotuner).
 // ---------------------------------------------------------------------------
 constexpr int kPipeThreads = 512;
-constexpr int kPipeProducerBar = 1;
+constexpr int kGatherPerLane = 4;  // node loads in flight per gathering lane
 
-// all NP producer threads arrive; true when pred holds on any of them
-template <int NP>
-__device__ __forceinline__ bool producers_any(bool pred) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((int)pred), "n"(kPipeProducerBar), "n"(NP)
-      : "memory");
-  return r != 0;
+// Shared-memory layout of the pipelined kernel (byte offsets from the start
+// of dynamic shared memory, or within a node buffer)
+struct PipeLayout {
+  uint32_t stage_bytes;                    // one stage (rows_layout without node data, 128-byte multiple)
+  uint32_t node_off;                       // node buffer 0 (buffer b at node_off + b node_bytes)
+  uint32_t node_bytes;                     // one node buffer:
+  uint32_t x_rel, ln_rel, rs_rel, gi_rel;  // coordinates, corner lists, row starts, node ids
+  uint32_t total;
+};
+
+__device__ __forceinline__ void pipe_fail(const RowsArgs& P, int* s_fail, int64_t blk) {
+  if (atomicExch(s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
 }
 
-template <int NP>
-__device__ __forceinline__ void producers_sync() {
-  asm volatile("bar.sync %0, %1;" ::"n"(kPipeProducerBar), "n"(NP) : "memory");
+// block blk's node data into node buffer nb, by one warp (lane = 0..31):
+// kGatherPerLane node ids per lane in flight, then their row starts and
+// coordinates, then the elements' corner lists (8 x 16 bits each)
+template <int D>
+__device__ __forceinline__ void pipe_gather(const RowsArgs& P, const PipeLayout& PL, int64_t blk,
+                                            unsigned char* nb, int lane) {
+  const RowBlock H = P.blocks[blk];
+  double* n_x = reinterpret_cast<double*>(nb + PL.x_rel);
+  int64_t* n_rs = reinterpret_cast<int64_t*>(nb + PL.rs_rel);
+  int32_t* n_gi = reinterpret_cast<int32_t*>(nb + PL.gi_rel);
+  const int32_t* lnodes = P.lnodes + H.lnode_off;
+  for (int t0 = 0; t0 < H.n_local; t0 += 32 * kGatherPerLane) {
+    int32_t node[kGatherPerLane];
+#pragma unroll
+    for (int k = 0; k < kGatherPerLane; ++k) {
+      const int t = t0 + 32 * k + lane;
+      node[k] = t < H.n_local ? lnodes[t] : -1;
+    }
+    int64_t rs[kGatherPerLane][D];
+    double x[kGatherPerLane][3];
+#pragma unroll
+    for (int k = 0; k < kGatherPerLane; ++k) {
+      const int64_t nd = node[k] < 0 ? 0 : node[k];
+#pragma unroll
+      for (int c = 0; c < D; ++c) rs[k][c] = node[k] < 0 ? 0 : P.row_ptr[(int64_t)D * nd + c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[k][c] = node[k] < 0 ? 0.0 : P.coords[3 * nd + c];
+    }
+#pragma unroll
+    for (int k = 0; k < kGatherPerLane; ++k) {
+      const int t = t0 + 32 * k + lane;
+      if (t < H.n_local) {
+        if (t < H.n_owned) {
+          n_gi[t] = node[k];
+#pragma unroll
+          for (int c = 0; c < D; ++c) n_rs[D * t + c] = rs[k][c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) n_x[3 * t + c] = x[k][c];
+      }
+    }
+  }
+  uint4* n_ln = reinterpret_cast<uint4*>(nb + PL.ln_rel);
+  for (int t = lane; t < H.n_helem; t += 32) n_ln[t] = reinterpret_cast<const uint4*>(P.helem_ln)[H.helem_off + t];
 }
 
 template <int OP, int PW>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-    k_block_pipe(const __grid_constant__ RowsArgs P, uint32_t stage_bytes) {
-  constexpr int kPipeProducers = 32 * PW;
-  constexpr int kPipeConsumers = kPipeThreads - kPipeProducers;
+    k_block_pipe(const __grid_constant__ RowsArgs P, const PipeLayout PL) {
+  constexpr int kProducers = 32 * PW;
+  constexpr int kConsumers = kPipeThreads - kProducers;
+  constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
   extern __shared__ __align__(128) unsigned char pipe_raw[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(pipe_raw + 2 * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(pipe_raw + 2 * PL.stage_bytes);
   uint64_t* empty = full + 2;
-  double* s_x = reinterpret_cast<double*>(pipe_raw + 2 * stage_bytes + 32);  // producers' node coordinates
+  uint64_t* ready = full + 4;  // three
   __shared__ int s_issued[2];
-  __shared__ int s_next[2];  // each stage's next batch of tasks
+  __shared__ int s_next[2];   // each stage's next batch of tasks
+  __shared__ int s_enext[2];  // each stage's next 4 elements
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
-    mbar_init_count(&full[0], kPipeProducers + 1);
-    mbar_init_count(&full[1], kPipeProducers + 1);
-    mbar_init_count(&empty[0], kPipeConsumers);
-    mbar_init_count(&empty[1], kPipeConsumers);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init_count(&full[k], kProducers + 1);
+      mbar_init_count(&empty[k], kConsumers);
+      s_issued[k] = 0;
+    }
+    for (int k = 0; k < 3; ++k) mbar_init_count(&ready[k], 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_issued[0] = s_issued[1] = 0;
     s_fail = 0;
   }
   __syncthreads();
-  const bool producer = threadIdx.x < kPipeProducers;
-  constexpr int D = OP == FEA_OP_DIFFUSION ? 1 : 3;
+  const int warp = threadIdx.x >> 5;
+  auto node_buf = [&](int i) { return pipe_raw + PL.node_off + (size_t)(i % 3) * PL.node_bytes; };
   int i = 0;
-  for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, ++i) {
-    const int s = i & 1;
-    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-    unsigned char* base = pipe_raw + (size_t)s * stage_bytes;
-    float* s_recs = reinterpret_cast<float*>(base + P.L.recs);
-    int64_t* s_rs = reinterpret_cast<int64_t*>(base + P.L.rs);
-    int32_t* s_gi = reinterpret_cast<int32_t*>(base + P.L.gi);
-    RowTask* s_tasks = reinterpret_cast<RowTask*>(base + P.L.tasks);
-    uint16_t* s_contrib = reinterpret_cast<uint16_t*>(base + P.L.contrib);
-    int32_t* s_hid = reinterpret_cast<int32_t*>(base + P.L.hid);
-    const RowBlock H = P.blocks[blk];
-    if (producer) {
-      // the consumers of block i - 2 have released this stage
-      const bool ok = i < 2 || mbar_wait_bounded(&empty[s], ph ^ 1u);
-      if (!ok && atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
-      // one decision for every producer; past this barrier, every producer has
-      // also finished reading the coordinate copy of the previous block
-      if (producers_any<kPipeProducers>(*((volatile int*)&s_fail) != 0)) break;
-      if (threadIdx.x == 0) {
-        s_next[s] = 0;  // published to the consumers by the arrival on full[s]
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
-        mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
-        if (H.task_bytes) bulk_copy_g2s(s_tasks, P.tasks + H.task_off, H.task_bytes, &full[s]);
-        if (H.contrib_bytes) bulk_copy_g2s(s_contrib, P.contrib + H.contrib_off, H.contrib_bytes, &full[s]);
-        if (H.helem_bytes) bulk_copy_g2s(s_hid, P.helem_id + H.helem_off, H.helem_bytes, &full[s]);
-        ++s_issued[s];
-      }
-      // the block's nodes (every one owns rows of a block-task plan): id, row
-      // starts and coordinates
-      const int32_t* lnodes = P.lnodes + H.lnode_off;
-      for (int t = threadIdx.x; t < H.n_local; t += kPipeProducers) {
-        const int32_t node = lnodes[t];
-        if (t < H.n_owned) {
-          s_gi[t] = node;
-#pragma unroll
-          for (int c = 0; c < D; ++c) s_rs[D * t + c] = P.row_ptr[(int64_t)D * node + c];
+  if (warp < PW) {
+    // the producers; warp 0 leads
+    const bool lead = warp == 0;
+    const int lane = threadIdx.x & 31;
+    if (lead && blockIdx.x < P.n_blocks) pipe_gather<D>(P, PL, blockIdx.x, node_buf(0), lane);
+    for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, ++i) {
+      const int s = i & 1;
+      if (*((volatile int*)&s_fail)) break;
+      if (lead) {
+        // the consumers have released this stage (block i - 2), and with it
+        // the producers are done with its records and counter
+        if (i >= 2 && !mbar_wait_bounded(&empty[s], ((uint32_t)(i >> 1) & 1u) ^ 1u)) {
+          if (lane == 0) pipe_fail(P, &s_fail, blk);
+          break;
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s_x[3 * t + c] = P.coords[3 * (int64_t)node + c];
+        if (lane == 0) {
+          const RowBlock H = P.blocks[blk];
+          unsigned char* base = pipe_raw + (size_t)s * PL.stage_bytes;
+          s_next[s] = 0;   // published to the consumers through full[s]
+          s_enext[s] = 0;  // and to the producers through ready[i % 3]
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the stage
+          mbar_expect_tx(&full[s], H.task_bytes + H.contrib_bytes + H.helem_bytes);
+          if (H.task_bytes) bulk_copy_g2s(base + P.L.tasks, P.tasks + H.task_off, H.task_bytes, &full[s]);
+          if (H.contrib_bytes)
+            bulk_copy_g2s(base + P.L.contrib, P.contrib + H.contrib_off, H.contrib_bytes, &full[s]);
+          if (H.helem_bytes) bulk_copy_g2s(base + P.L.hid, P.helem_id + H.helem_off, H.helem_bytes, &full[s]);
+          ++s_issued[s];
+        }
+        mbar_arrive(&ready[i % 3]);
+        // the next block's node data (its buffer was last read by block i - 2)
+        if (blk + gridDim.x < P.n_blocks) pipe_gather<D>(P, PL, blk + gridDim.x, node_buf(i + 1), lane);
       }
-      producers_sync<kPipeProducers>();
-      for (int h0 = 0; h0 < H.n_helem; h0 += kPipeProducers / 8) {
-        // a warp holds 4 elements; one with none left skips the pass (its
-        // modal transform would run on the FP64 pipe for nothing)
-        if (h0 + (int)((threadIdx.x & ~31u) >> 3) >= H.n_helem) continue;
-        const int h = h0 + (threadIdx.x >> 3);
-        const bool valid = h < H.n_helem;
+      if (!mbar_wait_bounded(&ready[i % 3], (uint32_t)(i / 3) & 1u)) {
+        pipe_fail(P, &s_fail, blk);
+        break;
+      }
+      const int n_helem = P.blocks[blk].n_helem;
+      const int64_t helem_off = P.blocks[blk].helem_off;
+      float* s_recs = reinterpret_cast<float*>(pipe_raw + (size_t)s * PL.stage_bytes + P.L.recs);
+      const unsigned char* nb = node_buf(i);
+      const double* n_x = reinterpret_cast<const double*>(nb + PL.x_rel);
+      const uint16_t* n_ln = reinterpret_cast<const uint16_t*>(nb + PL.ln_rel);
+      // a warp holds 4 elements (8 lanes each) and takes the next 4 when done
+      for (int h0 = grab_elements(&s_enext[s]); h0 < n_helem; h0 = grab_elements(&s_enext[s])) {
+        const int h = h0 + (lane >> 3);
+        const bool valid = h < n_helem;
         double v[3] = {0.0, 0.0, 0.0};
         if (valid) {
-          const int ln = P.helem_ln[8 * (H.helem_off + h) + hex8_corner_node(threadIdx.x & 7)];
+          const int ln = n_ln[8 * h + hex8_corner_node(threadIdx.x & 7)];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) v[c] = s_x[3 * ln + c];
+          for (int c = 0; c < 3; ++c) v[c] = n_x[3 * ln + c];
         }
-        hex_record<RecPipe>(P, valid, P.helem_id + H.helem_off + (valid ? h : 0), v,
+        hex_record<RecPipe>(P, valid, P.helem_id + helem_off + (valid ? h : 0), v,
                             s_recs + (size_t)(valid ? h : 0) * RecPipe::stride);
       }
       mbar_arrive(&full[s]);
-    } else {
+    }
+  } else {
+    // the consumers
+    for (int64_t blk = blockIdx.x; blk < P.n_blocks; blk += gridDim.x, ++i) {
+      const int s = i & 1;
       if (*((volatile int*)&s_fail)) break;
-      if (!mbar_wait_bounded(&full[s], ph)) {
-        if (atomicExch(&s_fail, 1) == 0) latch_error(P.st, FEA_ERR_TIMEOUT, (unsigned long long)blk);
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(i >> 1) & 1u)) {
+        pipe_fail(P, &s_fail, blk);
         break;
       }
-      run_tasks<OP, FEA_FP32_INTEGRATE, true, true, RecPipe>(P, H, s_recs, s_rs, s_tasks, s_contrib, s_hid, s_gi,
-                                                             (int)threadIdx.x - kPipeProducers, kPipeConsumers,
-                                                             &s_next[s]);
+      const RowBlock H = P.blocks[blk];
+      const unsigned char* base = pipe_raw + (size_t)s * PL.stage_bytes;
+      const unsigned char* nb = node_buf(i);
+      run_tasks<OP, FEA_FP32_INTEGRATE, true, true, RecPipe>(
+          P, H, reinterpret_cast<const float*>(base + P.L.recs), reinterpret_cast<const int64_t*>(nb + PL.rs_rel),
+          reinterpret_cast<const RowTask*>(base + P.L.tasks), reinterpret_cast<const uint16_t*>(base + P.L.contrib),
+          reinterpret_cast<const int32_t*>(base + P.L.hid), reinterpret_cast<const int32_t*>(nb + PL.gi_rel),
+          (int)threadIdx.x - kProducers, kConsumers, &s_next[s]);
       mbar_arrive(&empty[s]);
     }
   }
   __syncthreads();
   // after a timeout: let the bulk copies still in flight land before exit
   if (threadIdx.x == 0 && s_fail)
-    for (int s = 0; s < 2; ++s)
-      if (s_issued[s] > 0) mbar_wait_bounded(&full[s], (uint32_t)((s_issued[s] - 1) & 1));
+    for (int k = 0; k < 2; ++k)
+      if (s_issued[k] > 0) mbar_wait_bounded(&full[k], (uint32_t)((s_issued[k] - 1) & 1));
 }
 
 int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, double* A, double* b,
@@ -624,16 +708,23 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
   }
   if (geo) {
     RowsArgs Q = P;
-    Q.L = rows_layout(RP, true, RecPipe::stride);
-    const uint32_t stage_bytes = (Q.L.bar + 127u) & ~127u;
-    const size_t pipe_smem = 2 * (size_t)stage_bytes + 32 + 24 * (size_t)RP.max_local;
-    if (pipe_smem <= kRowsMaxSmem && RP.helem_ln != nullptr) {
+    Q.L = rows_layout(RP, true, RecPipe::stride, false);
+    PipeLayout PL;
+    PL.stage_bytes = (Q.L.bar + 127u) & ~127u;
+    PL.node_off = 2 * PL.stage_bytes + 64;  // after the seven mbarriers
+    PL.x_rel = 0;
+    PL.ln_rel = (24u * (uint32_t)RP.max_local + 15u) & ~15u;
+    PL.rs_rel = PL.ln_rel + 16u * (uint32_t)RP.max_helem;
+    PL.gi_rel = PL.rs_rel + 8u * (uint32_t)RP.ndof * (uint32_t)RP.max_owned;
+    PL.node_bytes = (PL.gi_rel + 4u * (uint32_t)RP.max_owned + 15u) & ~15u;
+    PL.total = PL.node_off + 3 * PL.node_bytes;
+    if (PL.total <= kRowsMaxSmem && RP.helem_ln != nullptr) {
       int dev = 0, sms = 0;
       FEA_CUDA(cudaGetDevice(&dev));
       FEA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       const unsigned grid = (unsigned)std::min<int64_t>(RP.n_blocks, sms);
       const bool dif = op->kind == FEA_OP_DIFFUSION;
-      void (*kern)(const RowsArgs, uint32_t) = nullptr;
+      void (*kern)(const RowsArgs, const PipeLayout) = nullptr;
       switch (m->pipe_producer_warps) {
         case 4: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 4> : k_block_pipe<FEA_OP_ELASTICITY, 4>; break;
         case 5: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 5> : k_block_pipe<FEA_OP_ELASTICITY, 5>; break;
@@ -641,8 +732,8 @@ int launch_task_kernel(const fea_operator* op, const RowsPlan& RP, const void* r
         case 8: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 8> : k_block_pipe<FEA_OP_ELASTICITY, 8>; break;
         default: kern = dif ? k_block_pipe<FEA_OP_DIFFUSION, 6> : k_block_pipe<FEA_OP_ELASTICITY, 6>; break;
       }
-      FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem));
-      kern<<<grid, kPipeThreads, pipe_smem, s>>>(Q, stage_bytes);
+      FEA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL.total));
+      kern<<<grid, kPipeThreads, PL.total, s>>>(Q, PL);
       FEA_CUDA(cudaGetLastError());
       return FEA_OK;
     }

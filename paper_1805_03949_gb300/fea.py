@@ -125,6 +125,7 @@ def _load():
         "fea_multidep_plan": (I32, [P, I32, ctypes.POINTER(I64), P, P, P, P]),
         "fea_multidep_hold": (I32, [P, I32, I32]),
         "fea_peak_probe": (I32, [I32, I64, ctypes.POINTER(ctypes.c_double), P]),
+        "fea_convert": (I32, [I32, P, P, I64, P]),
         "fea_mesh_set_pipe_split": (I32, [P, I32]),
         "fea_autotune": (I32, [ctypes.POINTER(fea_operator), P, P, P, P, P, I32, P, ctypes.POINTER(fea_tuning)]),
     }
@@ -527,6 +528,18 @@ def fea_peak_probe(kind: int, iters: int, stream=None) -> float:
     f = ctypes.c_double()
     _check(_lib.fea_peak_probe(int(kind), int(iters), ctypes.byref(f), _stream(stream)))
     return f.value
+
+
+def fea_convert(x: "torch.Tensor", stream=None) -> "torch.Tensor":
+    """The kernels' precision conversion of a CUDA tensor: float32 -> float64
+    (exact widening) or float64 -> float32 (round to nearest even)."""
+    if not isinstance(x, torch.Tensor) or x.dtype not in (torch.float32, torch.float64):
+        raise TypeError("fea_convert: a float32 or float64 CUDA tensor")
+    d = 0 if x.dtype == torch.float32 else 1
+    out = torch.empty(x.shape, dtype=torch.float64 if d == 0 else torch.float32, device=x.device)
+    _check(_lib.fea_convert(d, _dptr(x, x.dtype, name="x"), _dptr(out, out.dtype, x.numel(), "out"), x.numel(),
+                            _stream(stream)))
+    return out
 
 
 def fea_assemble_launches(op: "fea_operator", h) -> int:

@@ -101,6 +101,7 @@ def test_every_entry_point_rejects_a_null_handle(clib):
         "fea_assemble_launches": (None, None, ctypes.byref(k)),
         "fea_pack_lpt": (None, I64(1), 1, None, None, None),
         "fea_peak_probe": (0, I64(1000), None, None),
+        "fea_convert": (2, None, None, I64(0), None),
         "fea_mesh_set_pipe_split": (None, 6),
         "fea_autotune": (None, None, None, None, None, None, 3, None, None),
     }

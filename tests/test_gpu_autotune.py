@@ -98,3 +98,20 @@ def test_autotuned_configuration_matches_oracle(oracle, name, tmp_path):
         assert json.load(open(cache))[name][field] == t[field]
     finally:
         s.close()
+
+
+def test_assemble_refuses_misaligned_values():
+    """A must be 16-byte aligned (rows of complete entry blocks are written
+    with 16-byte stores); an offset view is refused before any work."""
+    import torch
+    fea = engine()
+    s = fea.System.from_mesh(mg.hex_cube(2, 0.0), 3)
+    try:
+        op = fea.make_operator(kind=1, precision=1, scatter=fea.FEA_SCATTER_BLOCK, poisson=0.3)
+        buf = torch.zeros(s.A.numel() + 1, dtype=torch.float64, device="cuda")
+        with pytest.raises(fea.FeaError):
+            fea.fea_assemble(op, s.handle, s.row_ptr, s.node_map, buf[1:], s.b)
+        s.assemble(op)
+        s.check()
+    finally:
+        s.close()
