@@ -627,6 +627,14 @@ struct PersistAsmArgs {
 template <int OP, int PREC>
 struct PersistCfg {
   static constexpr int S2 = (OP == FEA_OP_ELASTICITY && PREC == FEA_FP64) ? 2 : 1;
+  // CTAs per SM the any-type kernel is compiled for.  Its register count is
+  // the largest tile body's plus the call sequence (120 for FP32 diffusion),
+  // while the light types' own tiles need 46-56; measured on GB300 (4.53 M
+  // mixed elements, FP32 diffusion: 4.26 ms with no bound, 4.00 at 5, 3.90 at
+  // 6, 3.86 at 8; 256 elasticity meshes, FP32: 19.5 ms with no bound, 18.4
+  // at 5, 19.9 at 6, where spills start to cost more than the occupancy
+  // gains).  FP64 keeps the compiler's choice.
+  static constexpr int kMinBlocks = PREC == FEA_FP64 ? 1 : OP == FEA_OP_DIFFUSION ? 8 : 5;
   template <int TYPE, int SLOT, int SPLIT>
   static constexpr size_t bytes() { return sizeof(typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem); }
   static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
@@ -655,7 +663,8 @@ __device__ __noinline__ void persist_item_call(unsigned char* raw, const AsmPara
 // ONLY >= 0: every item uses that rule slot (a single-type mesh), so the
 // kernel holds one tile body and its register budget; -1: any element type
 template <int OP, int PREC, int ONLY>
-__global__ void __launch_bounds__(128) k_persistent(const __grid_constant__ PersistAsmArgs A) {
+__global__ void __launch_bounds__(128, ONLY < 0 ? PersistCfg<OP, PREC>::kMinBlocks : 1)
+    k_persistent(const __grid_constant__ PersistAsmArgs A) {
   constexpr int S2 = PersistCfg<OP, PREC>::S2;
   extern __shared__ __align__(16) unsigned char persist_smem[];
   __shared__ int s_item;
