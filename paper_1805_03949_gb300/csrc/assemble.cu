@@ -1171,7 +1171,14 @@ int assemble(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, const 
     if (rc) return rc;
   }
   if (nev > 0) FEA_CUDA(cudaEventRecord(ev[0], s));
-  FEA_CUDA(cudaMemsetAsync(A, 0, nnz * sizeof(double), s));
+  if (bplan) {
+    // the block-task kernels store every row whole except those of nodes on
+    // block boundaries, which they add to: only those rows are cleared
+    int rc = zero_block_rows(*bplan, row_ptr, A, s);
+    if (rc) return rc;
+  } else {
+    FEA_CUDA(cudaMemsetAsync(A, 0, nnz * sizeof(double), s));
+  }
   FEA_CUDA(cudaMemsetAsync(b, 0, m->n_nodes * D * sizeof(double), s));
   if (nev > 1) FEA_CUDA(cudaEventRecord(ev[1], s));
   if (op->scatter == FEA_SCATTER_BLOCK) {

@@ -12,7 +12,9 @@
 //     in the block (an interior entry: complete), or
 //   * added with an FP64 atomic if elements of other blocks add to it as well
 //     (a block-boundary entry, resolved globally).
-// A and b are zeroed first (boundary entries accumulate into them).
+// b and the rows of A that hold boundary entries (those of the nodes whose
+// elements lie in more than one block) are zeroed first; every other row of
+// A is written whole by stores.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -101,6 +103,27 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
     bstart.push_back(E);
   }
   const int64_t nb = (int64_t)bstart.size() - 1;
+  // the nodes whose elements lie in more than one block, as runs of
+  // consecutive ids: only their rows hold entries that several blocks add to
+  std::vector<int32_t> zero_runs;
+  {
+    std::vector<int32_t> blk_of(E);
+    for (int64_t b = 0; b < nb; ++b)
+      for (int64_t t = bstart[b]; t < bstart[b + 1]; ++t) blk_of[key[t] & 0xffffffffu] = (int32_t)b;
+    for (int64_t i = 0; i < N; ++i) {
+      bool shared = false;
+      for (int64_t u = incoff[i] + 1; u < incoff[i + 1] && !shared; ++u)
+        shared = blk_of[inc[u] >> 4] != blk_of[inc[incoff[i]] >> 4];
+      if (!shared) continue;
+      const size_t r = zero_runs.size();
+      if (r && zero_runs[r - 2] + zero_runs[r - 1] == i && zero_runs[r - 1] < kZeroRunNodes)
+        ++zero_runs[r - 1];
+      else {
+        zero_runs.push_back((int32_t)i);
+        zero_runs.push_back(1);
+      }
+    }
+  }
   std::vector<HostBlock> blocks(nb);
   unsigned nthreads = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<std::string> errors(nthreads);
@@ -195,7 +218,20 @@ int build_blocks_plan(fea_mesh* m, int ndof, int block_elems, cudaStream_t s, Ro
   for (auto& th : pool) th.join();
   for (auto& e : errors)
     if (!e.empty()) return fail(FEA_ERR_UNSUPPORTED, e);
-  return upload_plan(blocks, ndof, block_elems, block_elems, m->uniform && m->uniform_type == FEA_HEX8, out);
+  int rc = upload_plan(blocks, ndof, block_elems, block_elems, m->uniform && m->uniform_type == FEA_HEX8, out);
+  if (rc || zero_runs.empty()) return rc;
+  RowsPlan* R = *out;
+  const size_t zb = zero_runs.size() * sizeof(int32_t);
+  if (cudaMalloc((void**)&R->zero_runs, zb) != cudaSuccess ||
+      cudaMemcpy(R->zero_runs, zero_runs.data(), zb, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_rows_plan(R);
+    delete R;
+    *out = nullptr;
+    return fail(FEA_ERR_OOM, "block plan: cudaMalloc failed");
+  }
+  R->n_zero_runs = (int64_t)zero_runs.size() / 2;
+  R->bytes += zb;
+  return FEA_OK;
 }
 
 int ensure_blocks_plan(fea_mesh* m, int ndof, cudaStream_t s, RowsPlan** out) {

@@ -393,6 +393,9 @@ void free_rows_plan(RowsPlan* P) {
   cudaFree(P->helem_ln);
   cudaFree(P->tasks);
   cudaFree(P->contrib);
+  cudaFree(P->zero_runs);
+  P->zero_runs = nullptr;
+  P->n_zero_runs = 0;
   P->blocks = nullptr;
   P->lnodes = nullptr;
   P->helem_id = nullptr;

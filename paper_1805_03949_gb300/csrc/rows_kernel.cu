@@ -656,6 +656,36 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
   return rc;
 }
 
+// A warp per run of nodes: their rows of A, [row_ptr[D first], row_ptr[D
+// (first + count)]), are contiguous; zeroed with 16-byte stores (A is 16-byte
+// aligned), one 8-byte store at an odd start or end.
+__global__ void __launch_bounds__(256) k_zero_rows(const int32_t* runs, int64_t n_runs, const int64_t* row_ptr,
+                                                   int D, double* A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_runs; r += nwarps) {
+    const int64_t first = runs[2 * r], count = runs[2 * r + 1];
+    int64_t lo = row_ptr[(int64_t)D * first];
+    const int64_t hi = row_ptr[(int64_t)D * (first + count)];
+    if ((lo & 1) && lo < hi) {
+      if (lane == 0) A[lo] = 0.0;
+      ++lo;
+    }
+    const int64_t pairs = (hi - lo) >> 1;
+    double2* p = reinterpret_cast<double2*>(A + lo);
+    for (int64_t k = lane; k < pairs; k += 32) p[k] = make_double2(0.0, 0.0);
+    if (((hi - lo) & 1) && lane == 0) A[hi - 1] = 0.0;
+  }
+}
+
+int zero_block_rows(const RowsPlan& P, const int64_t* row_ptr, double* A, cudaStream_t s) {
+  if (P.n_zero_runs == 0) return FEA_OK;
+  const int64_t ctas = std::min<int64_t>((P.n_zero_runs + 7) / 8, 152 * 32);
+  k_zero_rows<<<(unsigned)ctas, 256, 0, s>>>(P.zero_runs, P.n_zero_runs, row_ptr, P.ndof, A);
+  FEA_CUDA(cudaGetLastError());
+  return FEA_OK;
+}
+
 bool fused_geometry(const fea_operator* op, const RowsPlan& RP) {
   return op->precision == FEA_FP32_INTEGRATE && RP.all_hex;
 }
