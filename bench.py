@@ -191,8 +191,10 @@ def algorithmic_flops_hex_elasticity(n_elems, n_nodes, nnz, nq=8, nn=8):
     """FP32 and FP64 arithmetic of one FP32-integrate hex8 elasticity assembly (FMA = 2 flop).
 
     FP64 geometry (per element): modal transform of the corners 3 stages x 8 x 3
-    adds; per point: Jacobian 9 entries x 3 FMA, cofactors 9 mul + 9 FMA, det
-    1 mul + 2 FMA, w det J 2 mul.
+    adds; the Jacobian's column c depends only on the other two coordinates
+    of the Gauss point, so it takes 4 distinct values over the 8 points: 3
+    columns x 4 values x 9 FMA per element; per point: cofactors 9 mul + 9
+    FMA, det 1 mul + 2 FMA, w det J 2 mul.
     FP64 accumulation: the contributions to one entry are FP32 and are summed
     in FP64, so an entry with k contributions takes at least k - 1 FP64 adds.
     A is symmetric, so only the (a <= b) blocks of every element count: 36 x 9
@@ -202,7 +204,7 @@ def algorithmic_flops_hex_elasticity(n_elems, n_nodes, nnz, nq=8, nn=8):
     block the moment g_a g_b^T, 9 FMA; RHS 3 FMA per (a, point); once per block
     lam M + mu M^T + mu tr(M) I, 33.
     """
-    geometry = 72 + nq * (2 * 27 + (9 + 2 * 9) + (1 + 2 * 2) + 2)
+    geometry = 72 + 2 * 108 + nq * ((9 + 2 * 9) + (1 + 2 * 2) + 2)
     blocks = nn * (nn + 1) // 2
     accumulate = (blocks * 9 * n_elems - (nnz + 9 * n_nodes) // 2) + (3 * nn * n_elems - 3 * n_nodes)
     fp32 = nq * ((2 * 72 + 24 + 3) + blocks * 2 * 9 + nn * 2 * 3) + blocks * 33
@@ -225,8 +227,10 @@ def element_flops(etype, op, nq, k_varies=False):
     geometry (FP64 in every precision): the Jacobian J, its cofactors C
       (9 mul + 9 FMA), det J (1 mul + 2 FMA) and w det J per point.
       hex8 (2x2x2 rule, modal form): 3 stages x 8 corners x 3 adds of the
-        Walsh-Hadamard transform of the corners; per point J from 4 modal
-        coefficients (9 entries x 3 FMA) and w det J (2 mul);
+        Walsh-Hadamard transform of the corners; J from 4 modal coefficients
+        per entry (3 FMA), column c at the 4 distinct pairs of the other two
+        point coordinates (3 x 4 x 9 FMA per element); w det J (2 mul) per
+        point;
       tet4 (affine): 3 x 3 edge differences, C, det and 1/det once; w det J
         (1 mul) per point;
       pyr5, prism6: 3 (nn - 1) differences to node 0 once; per point J = sum
@@ -256,7 +260,7 @@ def element_flops(etype, op, nq, k_varies=False):
     d = 1 if op == OP_DIFFUSION else 3
     affine = etype == 0
     if etype == 3:
-        geometry = 72 + nq * (2 * 27 + 27 + 5 + 2)
+        geometry = 72 + 2 * 108 + nq * (27 + 5 + 2)
     elif affine:
         geometry = 9 + 27 + 5 + 1 + nq
     else:
@@ -285,14 +289,15 @@ def j2_point_flops(plastic, iters):
     """FP64 arithmetic of the J2 update at one point beyond the geometry (FMA = 2, exp / div / sqrt = 1).
 
     displacement gradient from the modal form of the nodal displacements: J_u
-    (9 x 3 FMA), grad u = J_u C^T (27 FMA), times 1/det J (1 div + 9 mul);
+    (its columns shared by the points as J's: 108 FMA per element, 27 flop per
+    point), grad u = J_u C^T (27 FMA), times 1/det J (1 div + 9 mul);
     strain, trace and deviator 9; trial stress 2 mu (e_dev - eps_p) 12, its
     norm 13, sigma_y(alpha_n) 5, the yield test 2; an elastic point's stress
     4.  A plastic point adds 20 per Newton iteration (alpha, sigma_y and its
     slope with one exp, g, g', the update with one div) and 47 for the flow
     direction, stress, plastic strain, alpha and the tangent factors.
     """
-    base = 54 + 54 + 10 + 9 + 12 + 13 + 5 + 2
+    base = 27 + 54 + 10 + 9 + 12 + 13 + 5 + 2
     return base + (47 + 20 * iters if plastic else 4)
 
 

@@ -127,10 +127,23 @@ def counted_element(O, etype, X, op, tet_rule, k0=1.0, k2=0.0, f=(1.0, 1.0, 1.0)
         hex_pts = [((1 if q & 1 else -1) * g, (1 if q & 2 else -1) * g, (1 if q & 4 else -1) * g) for q in range(8)]
         shapes = [O.shape(3, p) for p in hex_pts]
         wq = [1.0] * 8
+        # column c of J depends only on the other two point coordinates: each
+        # of its 4 distinct values is formed once and shared by two points
+        cols = [{}, {}, {}]
+
+        def column(c, s, t):
+            if (s, t) not in cols[c]:
+                if c == 0:    # (y, z)
+                    cols[c][(s, t)] = [fma(v[7][i], s * t, fma(v[5][i], t, fma(v[3][i], s, v[1][i]))) for i in range(3)]
+                elif c == 1:  # (x, z)
+                    cols[c][(s, t)] = [fma(v[7][i], s * t, fma(v[6][i], t, fma(v[3][i], s, v[2][i]))) for i in range(3)]
+                else:         # (x, y)
+                    cols[c][(s, t)] = [fma(v[7][i], s * t, fma(v[6][i], t, fma(v[5][i], s, v[4][i]))) for i in range(3)]
+            return cols[c][(s, t)]
+
         for q, (x, y, z) in enumerate(hex_pts):
-            J = [[fma(v[7][i], y * z, fma(v[5][i], z, fma(v[3][i], y, v[1][i]))),
-                  fma(v[7][i], x * z, fma(v[6][i], z, fma(v[3][i], x, v[2][i]))),
-                  fma(v[7][i], x * y, fma(v[6][i], y, fma(v[5][i], x, v[4][i])))] for i in range(3)]
+            c0, c1, c2 = column(0, y, z), column(1, x, z), column(2, x, y)
+            J = [[c0[i], c1[i], c2[i]] for i in range(3)]
             C = _cofactors(J)
             det = _det(J, C)                       # det J' = 512 det J
             wdet = wq[q] * det * (1.0 / 512.0)     # 2 mul
