@@ -1274,6 +1274,9 @@ int assemble_launches(const fea_operator* op, const fea_mesh* m, int* n) {
     const bool fused = op->scatter == FEA_SCATTER_BLOCK && op->precision == FEA_FP32_INTEGRATE &&
                        m->group[FEA_HEX8].n == m->n_elems;
     *n = fused ? 1 : geometry_launches(m) + 1;
+    // block-task plans clear the rows of A they add to first (one kernel,
+    // unless the built plan has none: a mesh of one block)
+    if (op->scatter == FEA_SCATTER_BLOCK && !(m->blocks && m->blocks->n_zero_runs == 0)) *n += 1;
     return FEA_OK;
   }
   if (op->scatter == FEA_SCATTER_COLOR) {
