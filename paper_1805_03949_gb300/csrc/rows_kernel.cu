@@ -656,9 +656,14 @@ int assemble_rows(const fea_operator* op, fea_mesh* m, const int64_t* row_ptr, d
   return rc;
 }
 
+// 32 zero bytes at a 32-byte aligned address
+__device__ __forceinline__ void zero32(double* p) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %1, %1, %1};" ::"l"(__cvta_generic_to_global(p)), "d"(0.0) : "memory");
+}
+
 // A warp per run of nodes: their rows of A, [row_ptr[D first], row_ptr[D
-// (first + count)]), are contiguous; zeroed with 16-byte stores (A is 16-byte
-// aligned), one 8-byte store at an odd start or end.
+// (first + count)]), are contiguous; zeroed with 32-byte stores from the
+// first 32-byte boundary on, single values before it and after the last one.
 __global__ void __launch_bounds__(256) k_zero_rows(const int32_t* runs, int64_t n_runs, const int64_t* row_ptr,
                                                    int D, double* A) {
   const int lane = threadIdx.x & 31;
@@ -667,14 +672,14 @@ __global__ void __launch_bounds__(256) k_zero_rows(const int32_t* runs, int64_t 
     const int64_t first = runs[2 * r], count = runs[2 * r + 1];
     int64_t lo = row_ptr[(int64_t)D * first];
     const int64_t hi = row_ptr[(int64_t)D * (first + count)];
-    if ((lo & 1) && lo < hi) {
-      if (lane == 0) A[lo] = 0.0;
-      ++lo;
-    }
-    const int64_t pairs = (hi - lo) >> 1;
-    double2* p = reinterpret_cast<double2*>(A + lo);
-    for (int64_t k = lane; k < pairs; k += 32) p[k] = make_double2(0.0, 0.0);
-    if (((hi - lo) & 1) && lane == 0) A[hi - 1] = 0.0;
+    int64_t head = (int64_t)(((32u - ((uint32_t)(uintptr_t)(A + lo) & 31u)) & 31u) >> 3);
+    if (head > hi - lo) head = hi - lo;
+    if (lane < head) A[lo + lane] = 0.0;
+    lo += head;
+    const int64_t quads = (hi - lo) >> 2;
+    for (int64_t k = lane; k < quads; k += 32) zero32(A + lo + 4 * k);
+    const int64_t rest = (hi - lo) & 3;
+    if (lane < rest) A[lo + 4 * quads + lane] = 0.0;
   }
 }
 
