@@ -248,8 +248,8 @@ __device__ __forceinline__ void geometry_store(Smem& sm, const RefRule& rr, int 
     const float wdf = rr.wf[q] * detf * (float)(1.0 / (s * s * s));
     sm.W[le][q] = wdf;
     if constexpr (OP == FEA_OP_DIFFUSION) {
-      const float x = (float)xq;
-      sm.S[le][q] = wdf * ((float)P.k0 + (float)P.k2 * x * x);
+      const float x = f64_to_f32_rn(xq);
+      sm.S[le][q] = wdf * (f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x);
     } else {
       sm.S[le][q] = wdf;
     }
@@ -297,9 +297,9 @@ __device__ __forceinline__ bool geometry_fp32(Smem& sm, const RefRule& rr, int l
   float xr = 0.0f;
 #pragma unroll
   for (int a = 1; a < NN; ++a) {
-    const float d0 = (float)(sm.X[le][a][0] - sm.X[le][0][0]);
-    const float d1 = (float)(sm.X[le][a][1] - sm.X[le][0][1]);
-    const float d2 = (float)(sm.X[le][a][2] - sm.X[le][0][2]);
+    const float d0 = f64_to_f32_rn(sm.X[le][a][0] - sm.X[le][0][0]);
+    const float d1 = f64_to_f32_rn(sm.X[le][a][1] - sm.X[le][0][1]);
+    const float d2 = f64_to_f32_rn(sm.X[le][a][2] - sm.X[le][0][2]);
     xr += rr.Nf[q][a] * d0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -331,8 +331,8 @@ __device__ __forceinline__ bool geometry_fp32(Smem& sm, const RefRule& rr, int l
   const float wd = rr.wf[q] * det;
   sm.W[le][q] = wd;
   if constexpr (OP == FEA_OP_DIFFUSION) {
-    const float x = (float)sm.X[le][0][0] + xr;
-    sm.S[le][q] = wd * ((float)P.k0 + (float)P.k2 * x * x);
+    const float x = f64_to_f32_rn(sm.X[le][0][0]) + xr;
+    sm.S[le][q] = wd * (f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x);
   } else {
     sm.S[le][q] = wd;
   }
@@ -398,15 +398,7 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
         hex8_jacobian_pairs(sm.X[le], p, J);  // every lane: it exchanges columns with a partner lane
         if (valid) {
           double xq = 0.0;
-          if constexpr (OP == FEA_OP_DIFFUSION) {
-            const double g = 0.57735026918962576451;
-            const double xs = (p & 1) ? g : -g, ys = (p & 2) ? g : -g, zs = (p & 4) ? g : -g;
-            const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc = fma(sm.X[le][k][0], m[k], acc);
-            xq = 0.125 * acc;
-          }
+          if constexpr (OP == FEA_OP_DIFFUSION) xq = hex8_modal_x(sm.X[le], p);
           geometry_finish<OP, NN>(sm, rr, le, p, original_id(P, et), J, 8.0, xq, P);
         }
       }
@@ -628,14 +620,14 @@ __device__ __forceinline__ void tile_body(typename TileCfg<TYPE, SLOT, OP, PREC,
           if (run < 10 && ch < kRuns) {
             const int s = ch / PB, j = ch - PB * s;
             const int32_t k = ks[s * NB + part * PB + j];
-            if (k >= 0) red_add(P.A + rbs[s] + 3 * (int64_t)k + m, (double)vals[3 * ch + m]);
+            if (k >= 0) red_add(P.A + rbs[s] + 3 * (int64_t)k + m, widen(vals[3 * ch + m]));
           }
         }
       }
     }
     if (active)
 #pragma unroll
-      for (int c = 0; c < D; ++c) red_add(P.b + D * node + c, (double)rhs[c]);
+      for (int c = 0; c < D; ++c) red_add(P.b + D * node + c, widen(rhs[c]));
     __syncthreads();
     return;
   }

@@ -166,21 +166,78 @@ __device__ __forceinline__ void hex8_jacobian_pairs(const double (*c)[3], int q,
   }
 }
 
-// FP64 -> FP32, rounded to nearest even, with integer instructions (IEEE 754
-// binary64 to binary32): the 52-bit significand keeps its top 23 bits and
-// rounds up when the 29 dropped bits exceed half an ulp, or equal it with an
-// odd kept part; a carry out of the significand moves into the exponent,
-// which also gives the correct overflow to infinity.  Results outside the
-// normal binary32 range, zeros, infinities and NaNs take the hardware
-// conversion.  On GB300 the hardware conversion issues on the FP64 unit.
+// x coordinate at Gauss point q of the 2x2x2 rule from the modal
+// coefficients c_k of hex8_modal: (1/8) sum_k c_k prod_{s in k} xi_s, with
+// xi_s = +-1/sqrt(3) by bit s of q.  Each weight is (1/8) g^|k| with the sign
+// of the product (negative when an odd number of the bits of k are clear in
+// q), set by flipping the constant's sign bit with an integer XOR, so the sum
+// costs 8 FMAs and no FP64 multiply.  Equal to (1/8) times the sum with the
+// weights formed as products of +-g: the powers of g round the same way, and
+// the factor 1/8 is exact.
+__device__ __forceinline__ double hex8_modal_x(const double (*c)[3], int q) {
+  constexpr double g = 0.57735026918962576451;
+  constexpr double g2 = g * g, g3 = g2 * g;
+  constexpr double mag[8] = {0.125, 0.125 * g, 0.125 * g, 0.125 * g2, 0.125 * g, 0.125 * g2, 0.125 * g2, 0.125 * g3};
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int flip = (__popc(k & ~q) & 1) ? (int)0x80000000 : 0;
+    acc = fma(c[k][0], __hiloint2double(__double2hiint(mag[k]) ^ flip, __double2loint(mag[k])), acc);
+  }
+  return acc;
+}
+
+// FP64 -> FP32, rounded to nearest even, with integer instructions only
+// (IEEE 754 binary64 to binary32).  On GB300 the hardware conversion issues
+// on the FP64 unit, and a fallback to it for rare inputs was still issued by
+// every warp once the compiler predicated it (ncu: one FP64-pipe instruction
+// per conversion beyond the FP64 arithmetic), so no case uses it:
+// - a normal result (inline): the 52-bit significand keeps its top 23 bits
+//   and rounds up when the 29 dropped bits exceed half an ulp, or equal it
+//   with an odd kept part; a carry out of the significand moves into the
+//   exponent, which also gives the correct overflow to infinity;
+// - a zero or an FP64 subnormal (inline): a zero of the same sign;
+// - the rest, in a function of its own so that the common path stays a
+//   branch and not predicated code: a subnormal or zero binary32 result (the
+//   significand with its leading 1, shifted down to units of 2^-149 and
+//   rounded the same way; a carry into bit 23 is the smallest normal number's
+//   encoding), overflow to infinity, infinities, and NaNs (quiet, with the top
+//   bits of the payload).
+static __device__ __noinline__ float f64_to_f32_rare(uint32_t hi, uint32_t lo) {
+  const uint32_t sign = hi & 0x80000000u;
+  const int Ed = (int)((hi >> 20) & 0x7ffu);
+  if (Ed == 0x7ff) {
+    const uint32_t payload = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const bool nan = ((hi & 0xfffffu) | lo) != 0u;
+    return __uint_as_float(sign | 0x7f800000u | (nan ? (0x00400000u | payload) : 0u));
+  }
+  const int E = Ed - 896;
+  if (E >= 255) return __uint_as_float(sign | 0x7f800000u);
+  // value = M 2^(Ed - 1075) with M = 2^52 + fraction; in units of 2^-149 it
+  // is M 2^-(30 - E), a shift of at least 30; from 54 on the value is below
+  // half a unit and rounds to zero
+  const int sh = 30 - E;
+  if (sh >= 54) return __uint_as_float(sign);
+  const unsigned long long M = (((unsigned long long)(hi & 0xfffffu) | 0x100000ull) << 32) | lo;
+  const unsigned long long kept = M >> sh;
+  const unsigned long long rest = M & ((1ull << sh) - 1ull);
+  const unsigned long long half = 1ull << (sh - 1);
+  const uint32_t up = (rest > half) || (rest == half && (kept & 1ull));
+  return __uint_as_float(sign | ((uint32_t)kept + up));
+}
+
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (E <= 0 || E >= 255) return (float)x;
-  const uint32_t kept = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const uint32_t rest = lo & 0x1fffffffu;
-  const uint32_t up = (rest > 0x10000000u) || (rest == 0x10000000u && (kept & 1u));
-  return __uint_as_float(((hi & 0x80000000u) | ((uint32_t)E << 23) | kept) + up);
+  const int Ed = (int)((hi >> 20) & 0x7ffu);
+  const int E = Ed - 896;  // binary32 biased exponent
+  if (E > 0 && E < 255) {
+    const uint32_t kept = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;
+    const uint32_t up = (rest > 0x10000000u) || (rest == 0x10000000u && (kept & 1u));
+    return __uint_as_float(((hi & 0x80000000u) | ((uint32_t)E << 23) | kept) + up);
+  }
+  if (Ed == 0) return __uint_as_float(hi & 0x80000000u);
+  return f64_to_f32_rare(hi, lo);
 }
 
 // an FP64 value in the tile precision: exact for FP64 tiles, rounded to

@@ -88,8 +88,8 @@ __device__ __forceinline__ void geo_finish(const RefRule& rr, const GeoArgs& P, 
             (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * sc;
     rec[kRecW + q] = wdf;
     if (P.diffusion) {
-      const float x = (float)xq;
-      rec[kRecK + q] = (float)P.k0 + (float)P.k2 * x * x;
+      const float x = f64_to_f32_rn(xq);
+      rec[kRecK + q] = f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x;
     }
   }
 }
@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
     // adaptive: FP32 geometry on coordinates relative to node 0, distorted
     // elements flagged for the FP64 redo below
     if (valid && lane8 < NN) {
-      sD[le][lane8][0] = (float)(sX[le][lane8][0] - sX[le][0][0]);
-      sD[le][lane8][1] = (float)(sX[le][lane8][1] - sX[le][0][1]);
-      sD[le][lane8][2] = (float)(sX[le][lane8][2] - sX[le][0][2]);
+      sD[le][lane8][0] = f64_to_f32_rn(sX[le][lane8][0] - sX[le][0][0]);
+      sD[le][lane8][1] = f64_to_f32_rn(sX[le][lane8][1] - sX[le][0][1]);
+      sD[le][lane8][2] = f64_to_f32_rn(sX[le][lane8][2] - sX[le][0][2]);
     }
     __syncthreads();
     if (valid && q < NQ) {
@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
                 (R)((rr.dNf[q][a][0] * C[i][0] + rr.dNf[q][a][1] * C[i][1] + rr.dNf[q][a][2] * C[i][2]) * sc);
         rec[kRecW + q] = (R)wd;
         if (P.diffusion) {
-          const float x = (float)sX[le][0][0] + xr;
-          rec[kRecK + q] = (R)((float)P.k0 + (float)P.k2 * x * x);
+          const float x = f64_to_f32_rn(sX[le][0][0]) + xr;
+          rec[kRecK + q] = (R)(f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x);
         }
       }
     }
@@ -193,16 +193,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geometry(const __grid_constant_
       hex8_jacobian_pairs(sX[le], q, J);  // every lane: it exchanges columns with a partner lane
       if (valid) {
         double xq = 0.0;
-        if (P.diffusion) {
-          // x(xi_q) = x_0 + (1/8) sum_k c_k prod_{s in k} xi_s
-          const double g = 0.57735026918962576451;
-          const double xs = (q & 1) ? g : -g, ys = (q & 2) ? g : -g, zs = (q & 4) ? g : -g;
-          const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
-          double acc = 0.0;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) acc = fma(sX[le][k][0], m[k], acc);
-          xq = 0.125 * acc;
-        }
+        if (P.diffusion) xq = hex8_modal_x(sX[le], q);
         geo_finish<NN, PREC>(rr, P, q, id, J, 8.0, xq, rec);
       }
       return;

@@ -145,14 +145,8 @@ __device__ __forceinline__ void hex_record(const RowsArgs& P, bool valid, const 
           (P.hex.dNf[p][a][0] * Cf[i][0] + P.hex.dNf[p][a][1] * Cf[i][1] + P.hex.dNf[p][a][2] * Cf[i][2]) * sc;
   rec[L::w + p] = wdf;
   if (P.diffusion) {
-    const double g = 0.57735026918962576451;
-    const double xs = (p & 1) ? g : -g, ys = (p & 2) ? g : -g, zs = (p & 4) ? g : -g;
-    const double m[8] = {1.0, xs, ys, xs * ys, zs, xs * zs, ys * zs, xs * ys * zs};
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc = fma(c[k][0], m[k], acc);
-    const float x = (float)(0.125 * acc);
-    rec[L::k + p] = (float)P.k0 + (float)P.k2 * x * x;
+    const float x = f64_to_f32_rn(hex8_modal_x(c, p));
+    rec[L::k + p] = f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x;
   }
 }
 

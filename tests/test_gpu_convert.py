@@ -51,7 +51,13 @@ def test_rounding_is_nearest_even():
                      1.1754942e-38, 1.401298464324817e-45, 7.006492321624085e-46, 7.0e-46, 1e-50, 0.0, -0.0,
                      np.inf, -np.inf, np.nan, 1.0 + 2.0**-24, 1.0 + 3 * 2.0**-24, 1.0 - 2.0**-25],
                     dtype=np.float64).view(np.uint64)
-    b = np.concatenate([rnd, near, ends])
+    # results in the binary32 subnormal range: every multiple of 2^-150 up to
+    # 2^-138 (the odd ones are exact ties between neighbouring subnormals) and
+    # the doubles just above and below them, and random doubles there
+    k = np.ldexp(np.arange(-4096, 4097, dtype=np.float64), -150)
+    sub = np.concatenate([k, np.nextafter(k, np.inf), np.nextafter(k, -np.inf),
+                          np.ldexp(rng.uniform(-1.0, 1.0, size=4096), -126 - rng.integers(0, 26, size=4096))])
+    b = np.concatenate([rnd, near, ends, sub.view(np.uint64)])
     x = b.view(np.float64)
     got = fea.fea_convert(torch.from_numpy(x.copy()).cuda()).cpu().numpy()
     with np.errstate(over="ignore", invalid="ignore"):
