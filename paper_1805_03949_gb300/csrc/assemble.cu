@@ -428,12 +428,64 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
         cofactors(J, C);
         const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
         if (!(det > 0.0)) latch_error(P.st, FEA_ERR_INVERTED_ELEMENT, (unsigned long long)original_id(P, et));
+        if constexpr (PREC == FEA_FP64) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          double xq = sm.X[le][0][0];
+          for (int q = 0; q < NQ; ++q) {
+            double xq = sm.X[le][0][0];
 #pragma unroll
-          for (int a = 1; a < NN; ++a) xq += rr.N[q][a] * d[a][0];
-          geometry_store<OP, NN>(sm, rr, le, q, C, det, 1.0, xq, P);
+            for (int a = 1; a < NN; ++a) xq += rr.N[q][a] * d[a][0];
+            geometry_store<OP, NN>(sm, rr, le, q, C, det, 1.0, xq, P);
+          }
+        } else {
+          // FP32 tiles: the FP32 roundings of C, det J and x at the points
+          // replace the element's coordinates (read above), and the points'
+          // values follow with one thread per point
+          float xf[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            double xq = sm.X[le][0][0];
+#pragma unroll
+            for (int a = 1; a < NN; ++a) xq += rr.N[q][a] * d[a][0];
+            xf[q] = OP == FEA_OP_DIFFUSION ? f64_to_f32_rn(xq) : 0.0f;
+          }
+          float* o = reinterpret_cast<float*>(&sm.X[le][0][0]);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) o[3 * i + j] = f64_to_f32_rn(C[i][j]);
+          o[9] = f64_to_f32_rn(det);
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) o[10 + q] = xf[q];
+        }
+      }
+      if constexpr (PREC != FEA_FP64) {
+        static_assert(10 + NQ <= NN * 3 * 2, "C, det J and x_q must fit the element's coordinate slot");
+        __syncthreads();
+        for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
+          const int le = t / NQ, q = t % NQ;
+          if (e0 + le >= n_end) continue;
+          const float* o = reinterpret_cast<const float*>(&sm.X[le][0][0]);
+          float Cf[3][3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Cf[i][j] = o[3 * i + j];
+          const float detf = o[9];
+          const float inv = 1.0f / detf;
+#pragma unroll
+          for (int a = 0; a < NN; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              sm.G[le][q][a][i] =
+                  (rr.dNf[q][a][0] * Cf[i][0] + rr.dNf[q][a][1] * Cf[i][1] + rr.dNf[q][a][2] * Cf[i][2]) * inv;
+          const float wdf = rr.wf[q] * detf;
+          sm.W[le][q] = wdf;
+          if constexpr (OP == FEA_OP_DIFFUSION) {
+            const float x = o[10 + q];
+            sm.S[le][q] = wdf * (f64_to_f32_rn(P.k0) + f64_to_f32_rn(P.k2) * x * x);
+          } else {
+            sm.S[le][q] = wdf;
+          }
         }
       }
       __syncthreads();
