@@ -266,17 +266,18 @@ __device__ __forceinline__ void geometry_finish(Smem& sm, const RefRule& rr, int
   geometry_store<OP, NN>(sm, rr, le, q, C, det, s, xq, P);
 }
 
-// FP64 geometry of point q of element le, J from the node coordinates
-template <int OP, int NN, typename Smem>
+// FP64 geometry of point q of element le, J from the node coordinates (REL:
+// nodes 1 .. NN-1 hold their differences to node 0 already)
+template <int OP, int NN, bool REL = false, typename Smem>
 __device__ __forceinline__ void geometry_fp64(Smem& sm, const RefRule& rr, int le, int q, int64_t elem_id,
                                               const AsmParams& P) {
   double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double xq = sm.X[le][0][0];
 #pragma unroll
   for (int a = 1; a < NN; ++a) {
-    const double d0 = sm.X[le][a][0] - sm.X[le][0][0];
-    const double d1 = sm.X[le][a][1] - sm.X[le][0][1];
-    const double d2 = sm.X[le][a][2] - sm.X[le][0][2];
+    const double d0 = REL ? sm.X[le][a][0] : sm.X[le][a][0] - sm.X[le][0][0];
+    const double d1 = REL ? sm.X[le][a][1] : sm.X[le][a][1] - sm.X[le][0][1];
+    const double d2 = REL ? sm.X[le][a][2] : sm.X[le][a][2] - sm.X[le][0][2];
     xq += rr.N[q][a] * d0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -494,12 +495,20 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
   }
   // FP64 hex (modal) and tet tiles have returned above
   if constexpr (!(PREC == FEA_FP64 && (kModal || NN == 4))) {
+    if (all64) {
+      // the differences to node 0 once per element, not once per point
+      for (int t = threadIdx.x; t < EPC * (NN - 1) * 3; t += Cfg::THREADS) {
+        const int le = t / ((NN - 1) * 3), r = t % ((NN - 1) * 3);
+        if (e0 + le < n_end) sm.X[le][1 + r / 3][r % 3] -= sm.X[le][0][r % 3];
+      }
+      __syncthreads();
+    }
     for (int t = threadIdx.x; t < EPC * NQ; t += Cfg::THREADS) {
       const int le = t / NQ, q = t % NQ;
       const int64_t et = e0 + le;
       if (et >= n_end) continue;
       if (all64) {
-        geometry_fp64<OP, NN>(sm, rr, le, q, original_id(P, et), P);
+        geometry_fp64<OP, NN, true>(sm, rr, le, q, original_id(P, et), P);
       } else {
         if (!geometry_fp32<OP, NN>(sm, rr, le, q, P)) sm.flag[le] = 1;
       }

@@ -202,7 +202,9 @@ def test_cost_model_predicts_elastoplastic_item_costs(capsys):
         r2, res = _study(fea, s, dict(kind=fea.FEA_OP_J2, precision=1, u=u, state_in=st1), 32,
                          dict(u=u, state_in=st1), capsys, "J2 40^3")
         assert r2["mlp"] > r2["gauss_points"] + 0.2
-        assert res["mlp+steal"] < res["gauss_points+steal"], res
+        # the makespan gain is the largest-first order's (the LPT queues, with
+        # or without stealing, tie with the weights' within their quartiles)
+        assert res["mlp ordered"] < res["gauss_points ordered"], res
     finally:
         s.close()
 
