@@ -788,8 +788,13 @@ struct PersistCfg {
   // mixed elements, FP32 diffusion: 4.26 ms with no bound, 4.00 at 5, 3.90 at
   // 6, 3.86 at 8; 256 elasticity meshes, FP32: 19.5 ms with no bound, 18.4
   // at 5, 19.9 at 6, where spills start to cost more than the occupancy
-  // gains).  FP64 keeps the compiler's choice.
-  static constexpr int kMinBlocks = PREC == FEA_FP64 ? 1 : OP == FEA_OP_DIFFUSION ? 8 : 5;
+  // gains).  FP64 keeps the compiler's choice.  FP32 elasticity hex items
+  // scatter warp-cooperatively (CoopScatter), which needs 4 CTAs per SM: the
+  // 256 meshes 18.3 ms plain at 5, 19.3 cooperative at 5, 17.1 at 4, 18.8
+  // at 3.  The hex-only kernel (ONLY) keeps the plain scatter: cooperative,
+  // without a bound, it measured 8.56 against 7.46 ms on 2.1 M hexes.
+  static constexpr int kMinBlocks = PREC == FEA_FP64 ? 1 : OP == FEA_OP_DIFFUSION ? 8 : 4;
+  static constexpr bool kCoop = true;
   template <int TYPE, int SLOT, int SPLIT>
   static constexpr size_t bytes() { return sizeof(typename TileCfg<TYPE, SLOT, OP, PREC, SPLIT>::Smem); }
   static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
@@ -798,12 +803,13 @@ struct PersistCfg {
          mx(bytes<FEA_PRISM6, kRulePrism6, S2>(), bytes<FEA_HEX8, kRuleHex8, S2>()));
 };
 
-template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC = FEA_SCATTER_ATOMIC>
+template <int TYPE, int SLOT, int OP, int PREC, int SPLIT, int SC = FEA_SCATTER_ATOMIC, bool COOP = false>
 __device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams& P, int64_t first, int64_t end) {
   using Cfg = TileCfg<TYPE, SLOT, OP, PREC, SPLIT>;
   auto& sm = *reinterpret_cast<typename Cfg::Smem*>(raw);
+  constexpr bool kCoop = COOP && CoopScatter<Cfg, SC>::kOn;
   for (int64_t e0 = first; e0 < end; e0 += Cfg::EPC)
-    tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC>(sm, c_rules[SLOT], P, e0, end);
+    tile_body<TYPE, SLOT, OP, PREC, SPLIT, SC, kCoop>(sm, c_rules[SLOT], P, e0, end);
 }
 
 // One item of the any-type kernel, not inlined: the switch over five inlined
@@ -812,7 +818,7 @@ __device__ __forceinline__ void persist_item(unsigned char* raw, const AsmParams
 // occupancy; a call keeps the kernel near the largest body (96).
 template <int TYPE, int SLOT, int OP, int PREC, int SPLIT>
 __device__ __noinline__ void persist_item_call(unsigned char* raw, const AsmParams& P, int64_t first, int64_t end) {
-  persist_item<TYPE, SLOT, OP, PREC, SPLIT>(raw, P, first, end);
+  persist_item<TYPE, SLOT, OP, PREC, SPLIT, FEA_SCATTER_ATOMIC, PersistCfg<OP, PREC>::kCoop>(raw, P, first, end);
 }
 
 // ONLY >= 0: every item uses that rule slot (a single-type mesh), so the
