@@ -900,11 +900,11 @@ def workload_poisson(dev, pk, check, steps=20):
         s.close()
 
 
-def workload_hybrid(dev, pk, check, steps=5):
+def workload_hybrid(dev, pk, check, steps=5, n=100):
     """Hybrid tet/pyramid/prism/hex diffusion, k = 1 + x^2, degree-2 rules: per-type launches
     against one persistent launch over every type, scheduled by stealing or by packed queues."""
     from paper_1805_03949_gb300 import fea, meshgen as mg
-    mesh = mg.hybrid_cube(100, 3)
+    mesh = mg.hybrid_cube(n, 3)
     s = fea.System.from_mesh(mesh, 1, device=dev, with_cols=False)
     try:
         kw = dict(kind=0, tet_rule=1, k0=1.0, k2=1.0, source=1.0)
@@ -932,8 +932,8 @@ def workload_hybrid(dev, pk, check, steps=5):
         nnz_node = s.A.numel()
         roof = _rooflines(out, lambda k: assembly_work(_type_counts(mesh), mesh.n_nodes, nnz_node, OP_DIFFUSION,
                                                        0 if k.startswith("fp64") else 1, k_varies=True), pk)
-        res = {"workload": "hybrid 100^3 cube, 4,528,302 elements (tet 40 / pyr 10 / prism 20 / hex 30 %), "
-                           "diffusion k = 1 + x^2, degree-2 rules",
+        res = {"workload": f"hybrid {n}^3 cube, {mesh.n_elems:,} elements (tet 40 / pyr 10 / prism 20 / hex 30 % "
+                           "of the elements), diffusion k = 1 + x^2, degree-2 rules",
                "ms": out, "elements_per_s": {k: mesh.n_elems / (v * 1e-3) for k, v in out.items()}, "mlp": mlp,
                "roofline": roof}
         if check:
@@ -1076,7 +1076,12 @@ def other_workloads(args, dev, pk):
                     ("batch", workload_batch)):
         if key in wanted:
             t0 = time.perf_counter()
-            out[key] = fn(dev, pk, check, n=args.j2_n) if key == "j2" else fn(dev, pk, check)
+            if key == "j2":
+                out[key] = fn(dev, pk, check, n=args.j2_n)
+            elif key == "hybrid":
+                out[key] = fn(dev, pk, check, n=args.hybrid_n)
+            else:
+                out[key] = fn(dev, pk, check)
             out[key]["wall_s"] = time.perf_counter() - t0
             import torch
             torch.cuda.empty_cache()
@@ -1343,6 +1348,7 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="time the default launch parameters")
     ap.add_argument("--j2-n", type=int, default=96, help="cells per edge of the elastoplastic workload (96)")
+    ap.add_argument("--hybrid-n", type=int, default=100, help="cells per edge of the mixed-element workload (100)")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip every oracle step: the CPU baseline and the error of each result")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
