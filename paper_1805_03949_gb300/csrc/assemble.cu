@@ -605,6 +605,9 @@ struct CoopScatter {
     return 0;
   }
   static constexpr int PB = pb();
+  // hex8 with the 2x2x2 rule (PB = 4, 16-byte staging stores) is the tile it
+  // serves; staged in pairs of columns, the tet4 items of the 256-mesh batch
+  // made it slower (17.97 against 17.09 ms)
   static constexpr bool kOn = SC == FEA_SCATTER_ATOMIC && Cfg::D == 3 && Cfg::LPE == Cfg::NN && PB > 0 &&
                               std::is_same<typename Cfg::R, float>::value && kWarpBytes % 16 == 0 &&
                               (3 * PB) % 4 == 0;
