@@ -119,32 +119,18 @@ __device__ __forceinline__ void hex8_modal(double v[3]) {
   }
 }
 
-// J' = 8 J at Gauss point q (xi_s = +-1/sqrt(3) by bit s of q) from c[k][i];
-// the coordinate products are +-1/3 (the rounded square of the point), chosen
-// by sign so that they cost no FP64 multiply.
-__device__ __forceinline__ void hex8_jacobian(const double (*c)[3], int q, double J[3][3]) {
-  constexpr double g = 0.57735026918962576451;
-  constexpr double g2 = g * g;
-  const double x = (q & 1) ? g : -g, y = (q & 2) ? g : -g, z = (q & 4) ? g : -g;
-  const double xy = ((q ^ (q >> 1)) & 1) ? -g2 : g2;
-  const double xz = ((q ^ (q >> 2)) & 1) ? -g2 : g2;
-  const double yz = (((q >> 1) ^ (q >> 2)) & 1) ? -g2 : g2;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    J[i][0] = fma(c[7][i], yz, fma(c[5][i], z, fma(c[3][i], y, c[1][i])));
-    J[i][1] = fma(c[7][i], xz, fma(c[6][i], z, fma(c[3][i], x, c[2][i])));
-    J[i][2] = fma(c[7][i], xy, fma(c[6][i], y, fma(c[5][i], x, c[4][i])));
-  }
-}
-
-// The same J' for the lane's own point, with the work shared by the 8 lanes of
-// an element (lane p of an aligned group of 8 holds point p; every lane of the
-// warp must call it).  Column 0 depends only on (y, z) and column 1 only on
-// (x, z), so each takes 4 distinct values over the 8 points: lanes whose bits 0
-// and 1 agree form column 0, the others column 1, and each lane takes the
-// column it lacks from the partner with the same coordinates (lane p ^ 2 for
-// column 1, p ^ 1 for column 0).  Column 2 every lane forms itself.  18 FMAs
-// per point instead of 27, in the same order as hex8_jacobian (the same J).
+// J' = 8 J at Gauss point q (xi_s = +-1/sqrt(3) by bit s of q) from the modal
+// coefficients c[k][i] of hex8_modal, for the lane's own point, with the work
+// shared by the 8 lanes of an element (lane p of an aligned group of 8 holds
+// point p; every lane of the warp must call it).  Column j of J' is
+// sum_k c_k d(prod_{s in k} xi_s)/d xi_j, four terms; the coordinate products
+// are +-1/3 (the rounded square of the point), chosen by sign so that they
+// cost no FP64 multiply.  Column 0 depends only on (y, z) and column 1 only
+// on (x, z), so each takes 4 distinct values over the 8 points: lanes whose
+// bits 0 and 1 agree form column 0, the others column 1, and each lane takes
+// the column it lacks from the partner with the same coordinates (lane p ^ 2
+// for column 1, p ^ 1 for column 0).  Column 2 every lane forms itself: 18
+// FMAs per point instead of 27.
 __device__ __forceinline__ void hex8_jacobian_pairs(const double (*c)[3], int q, double J[3][3]) {
   constexpr double g = 0.57735026918962576451;
   constexpr double g2 = g * g;
@@ -285,11 +271,6 @@ __device__ __forceinline__ void red_add(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(g), "d"(v) : "memory");
 }
 
-// a request to bring the line holding p into L2; nothing is returned and
-// nothing waits for it
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
 
 // add into A or b: FP64 atomic (ATOMIC, Alg. "no coloring"), or a plain
 // read-modify-write when no other element of the launch touches the entry
