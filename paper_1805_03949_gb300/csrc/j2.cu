@@ -49,6 +49,7 @@ struct J2Params {
   double* stress_out;     // element loop: [E][8][6] Cauchy stress per point slot (may be nullptr)
   double lam, mu, kappa;
   double s0, sinf, delta, hard, tol_g, tol_step;
+  double mu2_3;           // 2 mu / 3: the factor 2 mu theta / 3 of an elastic point (theta = 1)
   int max_iter;
 };
 
@@ -98,7 +99,10 @@ __device__ __forceinline__ void j2_return(const J2Params& P, const double eps[6]
   for (int i = 0; i < 6; ++i) s[i] = 2.0 * P.mu * (e[i] - (i < 3 ? tr / 3.0 : 0.0));
   const double norm = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]));
   const double dsy = P.sinf - P.s0;
-  const double sy_n = P.s0 + P.hard * an + dsy * (1.0 - exp(-P.delta * an));
+  // sigma_y(alpha_n); at alpha_n = 0 (a point that never yielded) it is s0
+  // exactly, and the exp is not taken
+  double sy_n = P.s0;
+  if (an != 0.0) sy_n = P.s0 + P.hard * an + dsy * (1.0 - exp(-P.delta * an));
   r.theta = 1.0;
   r.theta_bar = 0.0;
   r.iters = 0;
@@ -247,7 +251,10 @@ __device__ __forceinline__ void j2_point(typename Cfg::Smem& sm, const RefRule& 
   }
   const double W = rr.w[q] * det * (1.0 / (s * s * s));
   sm.C[le][q][0] = to_tile<R>(W);
-  sm.C[le][q][1] = to_tile<R>(W * (P.kappa - 2.0 * P.mu * r.theta / 3.0));
+  // 2 mu theta / 3, from the host's 2 mu / 3 at an elastic point (the same
+  // value: theta = 1 there), so that point takes no FP64 division
+  const double mu2t_3 = r.yielded ? 2.0 * P.mu * r.theta / 3.0 : P.mu2_3;
+  sm.C[le][q][1] = to_tile<R>(W * (P.kappa - mu2t_3));
   sm.C[le][q][2] = to_tile<R>(W * P.mu * r.theta);
   sm.C[le][q][3] = to_tile<R>(W * 2.0 * P.mu * r.theta_bar);
 #pragma unroll
@@ -570,6 +577,7 @@ static J2Params j2_base_params(const fea_operator* op, fea_mesh* m, const int64_
   P.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   P.mu = E / (2.0 * (1.0 + nu));
   P.kappa = P.lam + 2.0 * P.mu / 3.0;
+  P.mu2_3 = 2.0 * P.mu / 3.0;
   P.s0 = op->sigma0;
   P.sinf = op->sigma_inf;
   P.delta = op->delta;
