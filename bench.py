@@ -602,14 +602,15 @@ def run_ours(args, rank, world, local_rank):
             b_h.copy_(b_d[j], non_blocking=True)
         done[j].record(cp)
 
-    # three timed windows of e2e_steps steps each, the median reported: one
-    # transient stall of the shared host link would otherwise set the figure
+    # five timed windows of e2e_steps steps each, the median reported: the
+    # host link is shared, and its rate into pinned memory was seen to halve
+    # for whole windows, which would otherwise set the figure
     e2e_steps = max(3, min(args.steps, 8))
     for k in range(2):
         e2e_step(k)
     torch.cuda.synchronize()
     windows = []
-    for _ in range(3):
+    for _ in range(5):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(comp)
         for k in range(e2e_steps):
