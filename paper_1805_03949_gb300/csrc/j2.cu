@@ -115,17 +115,22 @@ __device__ __forceinline__ void j2_return(const J2Params& P, const double eps[6]
     r.alpha = an;
     r.yielded = 0;
   } else {
-    double dg = 0.0;
+    double dg = 0.0, ex = 1.0;
     int it = 0, ok = 0;
+    bool ex_final = false;  // ex belongs to the final dg (no step after it)
     for (;;) {
       const double a = an + r23 * dg;
-      const double ex = exp(-P.delta * a);
+      ex = exp(-P.delta * a);
       const double g = norm - 2.0 * P.mu * dg - r23 * (P.s0 + P.hard * a + dsy * (1.0 - ex));
       if (fabs(g) <= P.tol_g * sy_n) {
         ok = 1;
+        ex_final = true;
         break;
       }
-      if (it == P.max_iter) break;
+      if (it == P.max_iter) {
+        ex_final = true;
+        break;
+      }
       const double gp = -2.0 * P.mu - (2.0 / 3.0) * (P.hard + dsy * P.delta * ex);
       const double step = -g / gp;
       dg += step;
@@ -138,7 +143,9 @@ __device__ __forceinline__ void j2_return(const J2Params& P, const double eps[6]
     r.iters = it;
     r.ok = ok;
     const double a = an + r23 * dg;
-    const double slope = P.hard + dsy * P.delta * exp(-P.delta * a);
+    // exp(-delta a) at the final dg: the loop's last value when it stopped at
+    // the residual test or the iteration limit (the same a), else a new one
+    const double slope = P.hard + dsy * P.delta * (ex_final ? ex : exp(-P.delta * a));
     const double inv = 1.0 / norm;
 #pragma unroll
     for (int i = 0; i < 6; ++i) r.n[i] = s[i] * inv;
