@@ -415,16 +415,18 @@ __device__ __forceinline__ void tile_geometry(typename Cfg::Smem& sm, const RefR
       for (int le = threadIdx.x; le < EPC; le += Cfg::THREADS) {
         const int64_t et = e0 + le;
         if (et >= n_end) continue;
-        double d[NN][3], J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        // with N = (1 - xi - eta - zeta, xi, eta, zeta) (ref_shape), dN_a/dxi_j
+        // is 1 for a = j + 1 and 0 for the other nodes past node 0: column j
+        // of J is the edge x_{j+1} - x_0, with no products
+        double d[NN][3], J[3][3];
 #pragma unroll
-        for (int a = 1; a < NN; ++a) {
+        for (int a = 1; a < NN; ++a)
 #pragma unroll
           for (int i = 0; i < 3; ++i) d[a][i] = sm.X[le][a][i] - sm.X[le][0][i];
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) J[i][j] += d[a][i] * rr.dN[0][a][j];
-        }
+          for (int j = 0; j < 3; ++j) J[i][j] = d[j + 1][i];
         double C[3][3];
         cofactors(J, C);
         const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
