@@ -119,7 +119,7 @@ __device__ __forceinline__ void hex_record(const RowsArgs& P, bool valid, const 
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[k][i] = __shfl_sync(0xffffffffu, v[i], base | k);
   double J[3][3];
-  hex8_jacobian_pairs(c, p, J);  // every lane (it exchanges columns)
+  hex8_jacobian_pairs<false>(c, p, J);  // every lane (it exchanges columns)
   if (!valid) return;
   double C[3][3];
   cofactors(J, C);
